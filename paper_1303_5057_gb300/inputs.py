@@ -1,0 +1,187 @@
+"""Seeded synthetic workloads for the Kerr photon tracer.
+
+This module only draws numbers: image-plane windows, spins, inclinations,
+image sizes, Poisson arrival times and, for the mixed workload, per-ray impact
+parameters.  It holds none of the tracer's arithmetic (no metric, no geodesic,
+no step rule, no pixel-centre rule) and is shared, unchanged, by the CUDA path's
+tests and benchmark and by the CPU oracle's tests.
+
+Random numbers come from splitmix64 (Steele, Lea & Flood 2014), mapped to
+doubles in [0, 1) by the top 53 bits, seeded with ``1303057 + workload index``.
+
+The workloads mirror the paper's: image-plane grids at r_obs = 1000 M
+(Sec. 3 grid projection, Sec. 4 photon-ring study), a 1024 x 1024 image
+(Sec. 5 discussion of image cost), and sweeps over spin and inclination
+(Sec. 4).  The paper uses no dataset.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 1303057
+_MASK = (1 << 64) - 1
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Outputs offset+1 .. offset+n of the splitmix64 sequence from ``seed``
+    (the generator is counter based, so any slice can be drawn directly)."""
+    with np.errstate(over="ignore"):
+        idx = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = (np.uint64(seed & _MASK) + idx * np.uint64(0x9E3779B97F4A7C15))
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, n: int, lo: float = 0.0, hi: float = 1.0, offset: int = 0) -> np.ndarray:
+    """n doubles uniform in [lo, hi) from splitmix64 (slice ``offset``)."""
+    u = (splitmix64(seed, n, offset) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+    return lo + (hi - lo) * u
+
+
+@dataclass
+class Image:
+    """One image request: a black hole of spin ``a`` seen by an observer at
+    ``r_obs`` and inclination ``incl`` (radians), through an nx x ny pixel grid
+    over [alpha0, alpha1] x [beta0, beta1] (units of M)."""
+    a: float
+    incl: float
+    nx: int
+    ny: int
+    r_obs: float = 1000.0
+    M: float = 1.0
+    alpha0: float = -10.0
+    alpha1: float = 10.0
+    beta0: float = -10.0
+    beta1: float = 10.0
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny
+
+
+@dataclass
+class Workload:
+    name: str
+    images: list = field(default_factory=list)
+    precision: str = "fp64"
+    max_steps: int = 100000
+
+    @property
+    def n_rays(self) -> int:
+        return sum(im.n for im in self.images)
+
+
+def schwarzschild_64():
+    """a = 0, i = 60 deg, 64 x 64 over [-10, 10]^2, FP64, cap 1e5 steps."""
+    return Workload("schwarzschild_a0_i60_64x64_fp64",
+                    [Image(a=0.0, incl=math.radians(60.0), nx=64, ny=64)],
+                    precision="fp64", max_steps=100000)
+
+
+def kerr_1024(side: int = 1024):
+    """a = 0.99, i = 90 deg, side x side over [-10, 10]^2, FP32 bulk with
+    selective FP64, cap 1e4 steps.  ``side`` < 1024 gives the same image at a
+    coarser resolution (same window) for CPU-sized parity runs."""
+    return Workload("kerr_a0.99_i90_%dx%d" % (side, side),
+                    [Image(a=0.99, incl=math.radians(90.0), nx=side, ny=side)],
+                    precision="fp32_kahan_sel64", max_steps=10000)
+
+
+def shadow_sweep(n_images: int = 256, side_lo: int = 64, side_hi: int = 1024,
+                 seed_index: int = 3):
+    """Batched sweep: n_images (a, i) pairs, a ~ U[0, 0.999], i ~ U[0, 90] deg,
+    square images of side ~ U{side_lo..side_hi} over [-10, 10]^2."""
+    s = SEED_BASE + seed_index
+    a = uniform(s, n_images, 0.0, 0.999)
+    inc = uniform(s + 101, n_images, 0.0, 90.0)
+    side = np.floor(uniform(s + 202, n_images, side_lo, side_hi + 1)).astype(int)
+    ims = [Image(a=float(a[k]), incl=math.radians(float(inc[k])), nx=int(side[k]),
+                 ny=int(side[k])) for k in range(n_images)]
+    return Workload("shadow_sweep_%d" % n_images, ims, precision="fp32_kahan_sel64",
+                    max_steps=10000)
+
+
+def _bardeen_point(a, incl, u):
+    """Point of the Kerr shadow boundary (Bardeen 1973, M = 1) at fraction u
+    between the prograde and retrograde circular photon orbits, per element.
+    Returns (alpha, beta >= 0, valid).  Used only to place near-critical rays."""
+    a = np.maximum(np.abs(a), 1e-6)
+    r_pro = 2.0 * (1.0 + np.cos(2.0 / 3.0 * np.arccos(-a)))
+    r_ret = 2.0 * (1.0 + np.cos(2.0 / 3.0 * np.arccos(a)))
+    rp = r_pro + u * (r_ret - r_pro)
+    xi = (rp * rp * (3.0 - rp) - a * a * (rp + 1.0)) / (a * (rp - 1.0))
+    eta = rp ** 3 * (4.0 * a * a - rp * (rp - 3.0) ** 2) / (a * a * (rp - 1.0) ** 2)
+    si = np.maximum(np.sin(incl), 1e-9)
+    ci = np.cos(incl)
+    al = -xi / si
+    b2 = eta + a * a * ci * ci - xi * xi * (ci / si) ** 2
+    ok = b2 >= 0.0
+    return al, np.sqrt(np.where(ok, b2, 0.0)), ok
+
+
+def mixed_rays(n: int = 1 << 26, seed_index: int = 2, offset: int = 0):
+    """Per-ray workload: rows (alpha, beta, a, incl, r_obs) for rays
+    offset .. offset+n-1 of the stream.  Even rays are uniform in |alpha|,
+    |beta| <= 20; odd rays lie within +-0.1 M (along the normal) of the
+    analytic shadow boundary for their own (a, i), where that boundary exists
+    at the drawn point (up to 8 redraws, else the ray stays uniform).
+    a ~ U[0, 0.999], i ~ U[0, 90] deg, r_obs = 1000."""
+    s = SEED_BASE + seed_index
+    a = uniform(s, n, 0.0, 0.999, offset)
+    inc = np.radians(uniform(s + 11, n, 0.0, 90.0, offset))
+    al = uniform(s + 22, n, -20.0, 20.0, offset)
+    be = uniform(s + 33, n, -20.0, 20.0, offset)
+    near = (np.arange(offset, offset + n) % 2) == 1
+    sgn = np.where(uniform(s + 55, n, offset=offset) < 0.5, -1.0, 1.0)
+    off = uniform(s + 66, n, -0.1, 0.1, offset)
+    todo = near.copy()
+    for attempt in range(8):
+        if not todo.any():
+            break
+        u = uniform(s + 44 + 1000 * attempt, n, 0.02, 0.98, offset)
+        pa, pb, ok = _bardeen_point(a, inc, u)
+        qa, qb, ok2 = _bardeen_point(a, inc, np.minimum(u + 1e-4, 1.0))
+        take = todo & ok & ok2
+        ta, tb = qa - pa, sgn * (qb - pb)
+        nrm = np.hypot(ta, tb)
+        nrm = np.where(nrm > 0, nrm, 1.0)
+        al = np.where(take, pa + off * (tb / nrm), al)
+        be = np.where(take, sgn * pb - off * (ta / nrm), be)
+        todo &= ~take
+    rays = np.empty((n, 5))
+    rays[:, 0] = al
+    rays[:, 1] = be
+    rays[:, 2] = a
+    rays[:, 3] = inc
+    rays[:, 4] = 1000.0
+    return rays
+
+
+@dataclass
+class Request:
+    rid: int
+    t_arrive: float
+    image: Image
+
+
+def request_stream(rate: float, n_requests: int, seed_index: int = 4,
+                   sides=(32, 64, 128, 256, 512, 1024, 2048)):
+    """Poisson arrivals at ``rate`` per second of render requests with side
+    uniform over ``sides``, a ~ U[0, 0.999], i ~ U[0, 90] deg, r_obs = 1000."""
+    s = SEED_BASE + seed_index + int(rate * 1000)
+    gaps = -np.log1p(-uniform(s, n_requests)) / rate
+    t = np.cumsum(gaps)
+    a = uniform(s + 1, n_requests, 0.0, 0.999)
+    inc = uniform(s + 2, n_requests, 0.0, 90.0)
+    pick = np.floor(uniform(s + 3, n_requests, 0, len(sides))).astype(int)
+    out = []
+    for k in range(n_requests):
+        side = int(sides[min(pick[k], len(sides) - 1)])
+        out.append(Request(k, float(t[k]), Image(a=float(a[k]), incl=math.radians(float(inc[k])),
+                                                  nx=side, ny=side)))
+    return out

@@ -1,0 +1,259 @@
+"""Closed forms from textbook general relativity, used to pin the oracle.
+
+Nothing here calls the oracle or the CUDA library; each function is an
+independent statement of a known result:
+
+* Schwarzschild Christoffel symbols (any GR text, e.g. Carroll Eq. 5.13 ff.);
+* the boundary of the Kerr shadow (Bardeen 1973), the critical curve the
+  paper's photon rings trace (Sec. 4);
+* the exact deflection of an equatorial Kerr photon as a one-dimensional
+  quadrature of the radial and azimuthal first integrals;
+* straight lines of flat space in (oblate) spheroidal coordinates, which is
+  what the Kerr metric becomes at M = 0.
+"""
+import math
+
+import numpy as np
+from scipy import integrate
+
+
+# ---------------------------------------------------------------------------
+# Schwarzschild
+# ---------------------------------------------------------------------------
+
+def schwarzschild_gamma(M, r, th):
+    """Nonzero Gamma^mu_ab (a <= b) of the Schwarzschild metric, keyed by
+    (mu, a, b) with indices t=0, r=1, theta=2, phi=3."""
+    f = 1.0 - 2.0 * M / r
+    s, c = math.sin(th), math.cos(th)
+    return {
+        (0, 0, 1): M / (r * r * f),
+        (1, 0, 0): M * f / (r * r),
+        (1, 1, 1): -M / (r * r * f),
+        (1, 2, 2): -r * f,
+        (1, 3, 3): -r * f * s * s,
+        (2, 1, 2): 1.0 / r,
+        (2, 3, 3): -s * c,
+        (3, 1, 3): 1.0 / r,
+        (3, 2, 3): c / s,
+    }
+
+
+def schwarzschild_deflection_series(M, b):
+    """Weak-field bending angle of light, to second order in M/b:
+    4M/b + 15 pi M^2 / (4 b^2)."""
+    return 4.0 * M / b + 15.0 * math.pi * M * M / (4.0 * b * b)
+
+
+# ---------------------------------------------------------------------------
+# Kerr shadow boundary (Bardeen 1973), M = 1
+# ---------------------------------------------------------------------------
+
+def photon_orbit_radii(a):
+    """Prograde and retrograde circular equatorial photon orbits."""
+    a = abs(a)
+    return (2.0 * (1.0 + math.cos(2.0 / 3.0 * math.acos(-a))),
+            2.0 * (1.0 + math.cos(2.0 / 3.0 * math.acos(a))))
+
+
+def bardeen_curve(a, incl, n=100000):
+    """Closed polygon (alpha, beta) of the shadow boundary seen at inclination
+    ``incl`` for spin ``a`` (M = 1), with the convention L_z / E = -alpha sin i.
+    a = 0 gives the circle of radius 3 sqrt 3."""
+    if abs(a) < 1e-12:
+        t = np.linspace(0.0, 2.0 * math.pi, n, endpoint=False)
+        R = 3.0 * math.sqrt(3.0)
+        return R * np.cos(t), R * np.sin(t)
+    r_pro, r_ret = photon_orbit_radii(a)
+    # cluster samples near both ends, where the curve meets beta = 0
+    u = 0.5 - 0.5 * np.cos(np.linspace(0.0, math.pi, n))
+    rp = r_pro + u * (r_ret - r_pro)
+    aa = abs(a)
+    xi = (rp * rp * (3.0 - rp) - aa * aa * (rp + 1.0)) / (aa * (rp - 1.0))
+    eta = rp ** 3 * (4.0 * aa * aa - rp * (rp - 3.0) ** 2) / (aa * aa * (rp - 1.0) ** 2)
+    si, ci = math.sin(incl), math.cos(incl)
+    al = -xi / si
+    b2 = eta + aa * aa * ci * ci - xi * xi * (ci / si) ** 2
+    ok = b2 >= 0.0
+    al, be = al[ok], np.sqrt(b2[ok])
+    if a < 0:  # (a, alpha) -> (-a, -alpha) symmetry
+        al = -al
+    # upper half then lower half reversed: a closed curve
+    A = np.concatenate([al, al[::-1]])
+    B = np.concatenate([be, -be[::-1]])
+    return A, B
+
+
+def polar_shadow_radius(a):
+    """Radius of the (circular) shadow seen from the spin axis, i = 0: the
+    spherical photon orbit with xi = L/E = 0 has sqrt(eta + a^2) as its
+    image radius (M = 1)."""
+    aa = abs(a)
+    if aa < 1e-12:
+        return 3.0 * math.sqrt(3.0)
+    lo, hi = photon_orbit_radii(aa)
+
+    def xi(r):
+        return (r * r * (3.0 - r) - aa * aa * (r + 1.0)) / (aa * (r - 1.0))
+
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if (xi(mid) > 0.0) == (xi(lo) > 0.0):
+            lo = mid
+        else:
+            hi = mid
+    r = 0.5 * (lo + hi)
+    eta = r ** 3 * (4.0 * aa * aa - r * (r - 3.0) ** 2) / (aa * aa * (r - 1.0) ** 2)
+    return math.sqrt(eta + aa * aa)
+
+
+def inside_polygon(px, py, cx, cy):
+    """Even-odd rule point-in-polygon test, vectorised over points."""
+    px = np.asarray(px, dtype=np.float64)
+    py = np.asarray(py, dtype=np.float64)
+    inside = np.zeros(px.shape, dtype=bool)
+    x0, y0 = cx, cy
+    x1, y1 = np.roll(cx, -1), np.roll(cy, -1)
+    for k in range(cx.size):
+        ya, yb = y0[k], y1[k]
+        if ya == yb:
+            continue
+        cond = (py >= min(ya, yb)) & (py < max(ya, yb))
+        xin = x0[k] + (py - ya) * (x1[k] - x0[k]) / (yb - ya)
+        inside ^= cond & (px < xin)
+    return inside
+
+
+def curve_distance(px, py, cx, cy):
+    """Distance from each point to the nearest sample of a dense curve."""
+    px = np.asarray(px, dtype=np.float64).ravel()
+    py = np.asarray(py, dtype=np.float64).ravel()
+    out = np.empty(px.size)
+    for i in range(0, px.size, 256):
+        dx = px[i:i + 256, None] - cx[None, :]
+        dy = py[i:i + 256, None] - cy[None, :]
+        out[i:i + 256] = np.sqrt((dx * dx + dy * dy).min(axis=1))
+    return out
+
+
+def shadow_truth(alpha, beta, a, incl, band=0.05, n_curve=100000):
+    """(inside, far) for each pixel: inside the analytic shadow, and farther
+    than ``band`` from its boundary.  For speed the polygon test uses a
+    decimated copy of the curve, which is safe away from the band."""
+    cx, cy = bardeen_curve(a, incl, n_curve)
+    d = curve_distance(alpha, beta, cx, cy)
+    step = max(1, cx.size // 4000)
+    inside = inside_polygon(alpha, beta, cx[::step], cy[::step])
+    return inside.reshape(np.shape(alpha)), (d > band).reshape(np.shape(alpha))
+
+
+# ---------------------------------------------------------------------------
+# Exact equatorial Kerr deflection (M = 1, E = 1, L_z = b)
+# ---------------------------------------------------------------------------
+
+def _radial_cubic(a, b):
+    """R(r) = (r^2 + a^2 - a b)^2 - Delta (b - a)^2 = r * C(r) with the cubic
+    C(r) = r^3 + (2a^2 - 2ab - (b - a)^2) r + 2 (b - a)^2."""
+    return np.array([1.0, 0.0, 2 * a * a - 2 * a * b - (b - a) ** 2, 2 * (b - a) ** 2])
+
+
+def turning_point(a, b):
+    roots = np.roots(_radial_cubic(a, b))
+    real = roots[np.abs(roots.imag) < 1e-9].real
+    return float(real.max())
+
+
+def equatorial_phi_integral(a, b, R):
+    """Signed azimuth swept from the turning point r_min out to radius R along
+    an equatorial photon of E = 1, L_z = b:
+        phi(R) - phi(r_min) = int_{r_min}^{R} [a (r^2 + a^2 - a b)/Delta + b - a] / sqrt(R(r)) dr
+    for the outgoing branch.  Substitution r = r_min + u^2 removes the
+    inverse square-root singularity at the turning point."""
+    c3 = _radial_cubic(a, b)
+    rm = turning_point(a, b)
+    # deflate the cubic: C(r) = (r - rm)(r^2 + p r + q)
+    p = c3[1] + rm
+    q = c3[2] + rm * p
+
+    def f(u):
+        r = rm + u * u
+        delta = r * r - 2.0 * r + a * a
+        num = a * (r * r + a * a - a * b) / delta + (b - a)
+        return 2.0 * num / math.sqrt(r * (r * r + p * r + q))
+
+    val, err = integrate.quad(f, 0.0, math.sqrt(R - rm), epsabs=1e-13, epsrel=1e-13, limit=400)
+    return val
+
+
+def equatorial_sweep(a, b, R_start, R_end):
+    """Total azimuth swept by an equatorial photon (E = 1, L_z = b) that comes
+    in from radius R_end, passes its turning point and leaves to R_start, in
+    the photon's forward direction."""
+    return equatorial_phi_integral(a, b, R_start) + equatorial_phi_integral(a, b, R_end)
+
+
+# ---------------------------------------------------------------------------
+# Flat space in Boyer-Lindquist (oblate spheroidal) coordinates, M = 0
+# ---------------------------------------------------------------------------
+
+def oblate_to_cart(a, r, th, ph):
+    rho = math.sqrt(r * r + a * a)
+    return np.array([rho * math.sin(th) * math.cos(ph),
+                     rho * math.sin(th) * math.sin(ph),
+                     r * math.cos(th)])
+
+
+def oblate_velocity(a, r, th, ph, kr, kth, kph):
+    """Cartesian velocity of (dr, dtheta, dphi) at (r, theta, phi)."""
+    rho = math.sqrt(r * r + a * a)
+    s, c = math.sin(th), math.cos(th)
+    cp, sp = math.cos(ph), math.sin(ph)
+    drho = r / rho
+    return np.array([
+        drho * kr * s * cp + rho * c * cp * kth - rho * s * sp * kph,
+        drho * kr * s * sp + rho * c * sp * kth + rho * s * cp * kph,
+        kr * c - r * s * kth,
+    ])
+
+
+def cart_to_oblate(a, X):
+    x, y, z = X
+    R2 = x * x + y * y + z * z
+    w = R2 - a * a
+    r2 = 0.5 * (w + math.sqrt(w * w + 4.0 * a * a * z * z))
+    r = math.sqrt(r2)
+    th = math.acos(max(-1.0, min(1.0, z / r)))
+    ph = math.atan2(y, x)
+    return r, th, ph
+
+
+def straight_line_exit(a, y0, r_exit):
+    """Follow the straight line through the state y0 (t, r, th, ph, k^t,
+    k^r, k^th, k^ph) backwards in the affine parameter and return (theta, phi)
+    where it leaves through the spheroid r = r_exit on the far side."""
+    X0 = oblate_to_cart(a, y0[1], y0[2], y0[3])
+    V = oblate_velocity(a, y0[1], y0[2], y0[3], y0[5], y0[6], y0[7])
+
+    def r_of(lam):
+        return cart_to_oblate(a, X0 + lam * V)[0]
+
+    # the closest approach is at lam_c = -(X0.V)/(V.V) < 0; the exit lies beyond
+    lam_c = -float(X0 @ V) / float(V @ V)
+    lo, hi = lam_c, lam_c
+    step = abs(lam_c) + 10.0
+    while r_of(hi) < r_exit:
+        hi -= step
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if r_of(mid) < r_exit:
+            lo = mid
+        else:
+            hi = mid
+    _, th, ph = cart_to_oblate(a, X0 + 0.5 * (lo + hi) * V)
+    return th, ph
+
+
+def angle_diff(x, y):
+    """x - y wrapped into (-pi, pi]."""
+    d = (np.asarray(x) - np.asarray(y) + math.pi) % (2.0 * math.pi) - math.pi
+    return d
