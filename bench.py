@@ -1,0 +1,331 @@
+"""Benchmark of the Kerr photon tracer on one GB300 (or N replicas).
+
+One step = one pass of the whole hot path over one image: image-plane set-up
+(FP64), backward RK4 trace of every ray to capture or escape, and render of
+the per-pixel results.  Workload: a = 0.99, i = 90 deg, r_obs = 1000 M,
+1024 x 1024 pixels over [-10, 10]^2 M, compensated FP32 with double steps
+near the horizon, at most 1e4 steps per ray.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the host cores instead, on a bounded sample of the same workload.
+
+Multi-GPU: rays are independent, so N GPUs run N independent replicas of the
+workload (weak scaling, no collective on the data path); the timing is the
+maximum over ranks and the value is the sum of the work of all ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "photon RK4 steps/s FP32 vs FP64, 1 GB300; p50/p99 image-request latency"
+UNIT = "photon-steps/s"
+
+# Algorithmic work of one accepted step of the compensated FP32 path, counted
+# on the closed-form source (FMA = 2 flops, add/mul = 1; each divide and each
+# sincos counted as 1 flop and listed apart): 4 right-hand sides x 109, stage
+# states 37, RK4 combination 41, compensated update 32, Eq. 4 monitor 39,
+# step rule 6.
+F_STEP = 591
+SPECIAL_PER_STEP = {"sincos": 5, "div": 15}
+# FP32 non-tensor peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz.
+SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0
+# FP64 non-tensor: 2 FP64 lanes per SM on this part.
+FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1000.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gray", choices=["gray", "reference"])
+    p.add_argument("--side", type=int, default=1024)
+    p.add_argument("--precision", default="fp32_kahan_sel64")
+    p.add_argument("--r-sw", type=float, default=0.25)
+    p.add_argument("--step-rule", default="bench", choices=["bench", "eq2"])
+    p.add_argument("--block", type=int, default=0)
+    p.add_argument("--blocks-per-sm", type=int, default=0)
+    p.add_argument("--refill", type=int, default=0)
+    p.add_argument("--no-fp64-leg", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-rays", type=int, default=16384)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ clocks ---
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples taken while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+# ------------------------------------------------------------- CPU oracle ---
+
+def cpu_sample_rays(im, n_sample):
+    """A seeded, evenly spread subset of the image's pixels (alpha, beta)."""
+    from oracle import oracle as O
+    al, be = O.pixel_centres(im.nx, im.ny, im.alpha0, im.alpha1, im.beta0, im.beta1)
+    n = al.size
+    idx = np.unique(np.linspace(0, n - 1, min(n_sample, n)).astype(np.int64))
+    rays = np.empty((idx.size, 5))
+    rays[:, 0], rays[:, 1] = al[idx], be[idx]
+    rays[:, 2], rays[:, 3], rays[:, 4] = im.a, im.incl, im.r_obs
+    return rays
+
+
+def cpu_oracle_rate(im, max_steps, step_rule, n_sample):
+    import oracle
+    rays = cpu_sample_rays(im, n_sample)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    out = oracle.trace_many(rays, oracle.Options(max_steps=max_steps, step_rule=step_rule), nthreads=cores)
+    dt = time.perf_counter() - t0
+    steps = float(out[:, 1].sum())
+    return steps / dt, cores, rays.shape[0], steps, dt
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle, as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1303_5057_gb300 import inputs as I
+    im = I.kerr_1024(args.side).images[0]
+    rule = 1 if args.step_rule == "eq2" else 0
+    per_step = max(256, args.cpu_rays // 4)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(im, 10000, rule, per_step)
+    rates, steps_all, t_all = [], 0.0, 0.0
+    cores = os.cpu_count() or 1
+    for _ in range(args.steps):
+        r, cores, n, st, dt = cpu_oracle_rate(im, 10000, rule, per_step)
+        rates.append(r)
+        steps_all += st
+        t_all += dt
+    value = steps_all / t_all
+    sample = "%d evenly spread pixels of the %dx%d image per step" % (per_step, args.side, args.side)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_all / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "kerr_a0.99_i90_%dx%d" % (args.side, args.side), "rays": args.side ** 2,
+                       "max_steps": 10000, "step_rule": args.step_rule},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm ---
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    from paper_1303_5057_gb300 import build, gray
+    from paper_1303_5057_gb300 import inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    gray.lib()
+
+    prec = gray.PRECISIONS[args.precision]
+    rule = gray.STEP_EQ2 if args.step_rule == "eq2" else gray.STEP_BENCH
+    im = I.kerr_1024(args.side).images[0]
+    n = im.n
+    opt = gray.Options(precision=prec, max_steps=10000, r_sw=args.r_sw, step_rule=rule, block=args.block,
+                       blocks_per_sm=args.blocks_per_sm, refill=args.refill)
+    tr = gray.Tracer(opt, n)
+    stream = torch.cuda.current_stream()
+    out_dev = torch.empty(16 * n, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def one_step():
+        tr.setup([im])
+        tr.trace(wait=False)
+        tr.render(gray.RENDER_PIXELS32, out=out_dev)
+
+    # warm-up; the last warm-up step also reads the step statistics
+    for _ in range(max(args.warmup, 1)):
+        one_step()
+    tr.setup([im])
+    _, _, stats = tr.trace()
+    steps_per_pass = stats[0]
+    fp64_steps = stats[2]
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(torch.cuda.current_device())
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = gray.gray_launch_count()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        e0, e1, e2, e3 = ev[k]
+        e0.record(stream)
+        tr.setup([im])
+        e1.record(stream)
+        tr.trace(wait=False)
+        e2.record(stream)
+        tr.render(gray.RENDER_PIXELS32, out=out_dev)
+        e3.record(stream)
+    torch.cuda.synchronize()
+    launches = gray.gray_launch_count() - launches0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(d) for a, b, c, d in ev]
+    trace_ms = [b.elapsed_time(c) for a, b, c, d in ev]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * steps_per_pass * args.steps / (total_ms / 1000.0)
+    trace_avg_s = statistics.mean(trace_ms) / 1000.0
+    achieved = F_STEP * steps_per_pass / trace_avg_s / 1e12
+
+    # ---- end to end through the C ABI: host image table in, pixels out to pinned host ----
+    host_out = torch.empty(16 * n, dtype=torch.uint8, pin_memory=True)
+    e2e_ms = []
+    for k in range(max(1, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tr.setup([im])
+        tr.trace(wait=False)
+        tr.render(gray.RENDER_PIXELS32, out=out_dev)
+        host_out.copy_(out_dev, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+    e2e_value = steps_per_pass / (statistics.mean(e2e_ms) / 1000.0) * world
+
+    # ---- plain FP64 GPU path on the same image (the speed reference) ----
+    fp64 = None
+    if not args.no_fp64_leg and rank == 0:
+        tr64 = gray.Tracer(gray.Options(precision=gray.FP64, max_steps=10000, step_rule=rule), n)
+        tr64.setup([im])
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tr64.trace(wait=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b)
+        tr64.setup([im])
+        _, _, st64 = tr64.trace()
+        tr64.close()
+        fp64 = {"value": st64[0] / (ms64 / 1000.0), "unit": UNIT, "trace_ms": ms64,
+                "roofline_frac_fp64": F_STEP * st64[0] / (ms64 / 1000.0) / 1e12 / FP64_PEAK_TFLOPS}
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        rate, cores, ns, st, dt = cpu_oracle_rate(im, 10000, 1 if rule == gray.STEP_EQ2 else 0, args.cpu_rays)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d evenly spread pixels of the %dx%d image (%.0f steps, %.1f s)" % (
+                   ns, args.side, args.side, st, dt)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "kerr_a0.99_i90_%dx%d_%s" % (args.side, args.side, args.precision),
+                       "rays": n, "max_steps": 10000, "step_rule": args.step_rule, "r_sw": args.r_sw,
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "ns_per_photon_step": 1e9 / (value / world),
+            "steps_per_pass": steps_per_pass, "fp64_steps_per_pass": fp64_steps,
+            "trace_ms": statistics.mean(trace_ms),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (FP32 non-tensor, max clock)",
+                         "flop_per_step": F_STEP, "special_per_step": SPECIAL_PER_STEP},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 72, "d2h_bytes_per_step": 16 * n},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "fp64_gpu": fp64,
+            "speedup_vs_fp64_gpu": (value / world) / fp64["value"] if fp64 else None,
+        }
+        print(json.dumps(line), flush=True)
+    tr.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,228 @@
+/*
+ * gray.h -- C ABI of libgray, a GB300 (sm_103a) tracer of photons along null
+ * geodesics of the Kerr metric, after Chan, Psaltis & Ozel 2013, "GRay: a
+ * Massively Parallel GPU-Based Code for Ray Tracing in Relativistic
+ * Spacetimes".
+ *
+ * The method (Sec. 2): one photon per GPU thread; the second-order geodesic
+ * equation d^2 x^mu / d l^2 = -Gamma^mu_ab k^a k^b in Boyer-Lindquist
+ * coordinates is integrated with classic RK4, with the step size of Eq. 2
+ * (or the benchmark rule |h| = max(min(f r, (r - r_h) / (2 |k^r|)), h_min)),
+ * the null-norm monitor xi of Eq. 4 with a forward-Euler redo at h/9, the pole
+ * remap of Eq. 3, and a stop at the horizon or at escape.  Photons start on an
+ * image plane at distance r_obs and inclination i (Sec. 4) and are traced
+ * backward in the affine parameter.
+ *
+ * Conventions for every call:
+ *   - Units G = c = 1; lengths in units of M.  Angles in radians.
+ *   - Buffers named *_dev are device pointers owned by the caller; buffers
+ *     named *_host are host pointers owned by the caller.  The library owns
+ *     only the gray_ctx and the small device workspace inside it.
+ *   - Every call that takes a stream enqueues its work on that stream
+ *     (cudaStream_t passed as void*; NULL = legacy default stream) and
+ *     returns without waiting, unless a host output pointer is given.
+ *   - A gray_ctx may be used by one host thread and one stream at a time.
+ *   - Return value 0 = success; negative values are errors (GRAY_E*), never
+ *     exceptions; gray_trace returns a positive value when rays remain
+ *     active after the step budget (not an error).
+ */
+#ifndef GRAY_H
+#define GRAY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes --------------------------------------------------- */
+#define GRAY_OK 0
+#define GRAY_EINVAL (-1)   /* bad argument: NaN or out-of-range parameter, n < 0, buffer too small */
+#define GRAY_ECUDA (-2)    /* a CUDA runtime call failed (launch, copy, memset) */
+#define GRAY_ENOMEM (-3)   /* host or device allocation of the context failed */
+
+/* ---- per-ray status (the paper's stop conditions, Sec. 2) ----------- */
+#define GRAY_RAY_ACTIVE 0    /* still being traced */
+#define GRAY_RAY_CAPTURED 1  /* reached r <= cap_frac * r_h (horizon stop) */
+#define GRAY_RAY_ESCAPED 2   /* reached r >= r_esc moving outward along the trace */
+#define GRAY_RAY_STEP_CAP 3  /* hit max_steps */
+#define GRAY_RAY_NONFINITE 4 /* state became NaN or Inf */
+
+/* ---- arithmetic of the trace ---------------------------------------- */
+#define GRAY_FP64 0             /* every step in double precision */
+#define GRAY_FP32 1             /* every step in single precision */
+#define GRAY_FP32_KAHAN 2       /* single precision, compensated (Kahan) state update */
+#define GRAY_FP32_KAHAN_SEL64 3 /* as GRAY_FP32_KAHAN, with steps near the horizon promoted to double */
+
+/* ---- step-size rule ------------------------------------------------- */
+#define GRAY_STEP_BENCH 0 /* |h| = max(min(h_frac r, (r - r_h)/(2|k^r|)), h_min) */
+#define GRAY_STEP_EQ2 1   /* Eq. 2: min(h_frac / (|k^r/r| + |k^th| + |k^ph|), (r - r_h)/(2|k^r|)), floored at h_min */
+
+/* ---- render kinds ---------------------------------------------------- */
+#define GRAY_RENDER_PIXELS64 0   /* per ray gray_pixel64 */
+#define GRAY_RENDER_PIXELS32 1   /* per ray gray_pixel32 */
+#define GRAY_RENDER_RECORD 3     /* per ray 17 doubles, see gray_render */
+#define GRAY_RENDER_INVARIANTS 4 /* per ray 4 doubles (E, L_z, Q, g k k) of the stored state */
+
+/* ---- device unit evaluations (gray_eval) ----------------------------- */
+#define GRAY_EVAL_CHRISTOFFEL 0 /* in (M, a, r, th) -> out Gamma^mu_ab, 64 values, [mu][a][b] */
+#define GRAY_EVAL_RHS 1         /* in (M, a, y[8]) -> out dy/dl, 8 values */
+#define GRAY_EVAL_INITIAL 2     /* in (M, a, r_obs, incl, alpha, beta) -> out y[8] */
+#define GRAY_EVAL_XI 3          /* in (M, a, y[8]) -> out xi of Eq. 4, 1 value */
+
+/* One image: a hole of spin a and mass M seen by an observer at distance
+ * r_obs and inclination incl, through an nx x ny grid of pixel centres
+ * alpha_j = alpha0 + (j + 1/2)(alpha1 - alpha0)/nx (beta likewise) on the
+ * image plane (Sec. 4 sets the plane at r = 1000 M).  Ray index within the
+ * image is row * nx + column, rows along beta. */
+typedef struct gray_image {
+    double a;        /* spin; |a| < M when M > 0, any |a| when M = 0 (flat space) */
+    double M;        /* mass, >= 0 */
+    double r_obs;    /* distance of the image plane, > 0 */
+    double incl;     /* observer inclination, radians, [0, pi] */
+    int32_t nx, ny;  /* pixels, >= 1 each */
+    double alpha0, alpha1, beta0, beta1; /* window on the image plane */
+} gray_image;
+
+/* Integration options (Sec. 2 parameters plus the GPU launch shape). */
+typedef struct gray_options {
+    int32_t precision;     /* GRAY_FP64 ... GRAY_FP32_KAHAN_SEL64 */
+    int32_t step_rule;     /* GRAY_STEP_BENCH or GRAY_STEP_EQ2 */
+    int32_t max_steps;     /* per-ray cap over all gray_trace calls, >= 1 */
+    int32_t block;         /* threads per block of the trace kernel (multiple of 32, 32..1024), 0 = default */
+    int32_t blocks_per_sm; /* resident blocks per SM of the persistent grid, 0 = default */
+    int32_t refill;        /* steps between warp refills from the work queue, 0 = default */
+    double h_frac;         /* 1/32: the f of the benchmark rule, the Delta of Eq. 2 */
+    double h_min;          /* 1e-3: floor on |h| */
+    double cap_frac;       /* 1.01: capture when r <= cap_frac * r_h */
+    double eps_xi;         /* 1e-3: Euler redo when |xi + 1| > eps_xi (Eq. 4) */
+    double r_esc_frac;     /* 1.0: escape radius = r_esc_frac * r_obs */
+    double r_sw;           /* GRAY_FP32_KAHAN_SEL64: steps with r < cap_frac r_h + r_sw run in double */
+} gray_options;
+
+/* Per-ray output of GRAY_RENDER_PIXELS64: final position on the stop
+ * surface (interpolated within the last step) and the ray's status. */
+typedef struct gray_pixel64 {
+    double r, theta, phi;
+    int32_t status, steps;
+} gray_pixel64;
+
+/* Per-ray output of GRAY_RENDER_PIXELS32. */
+typedef struct gray_pixel32 {
+    float r, theta, phi;
+    int32_t status;
+} gray_pixel32;
+
+/* Per-image output of gray_shadow: pixels whose ray was captured,
+ * their area on the image plane, the radius sqrt(area/pi) of the disc of
+ * equal area, and the mean (alpha, beta) of the captured pixels. */
+typedef struct gray_shadow_info {
+    int64_t n_captured, n_escaped, n_other;
+    double area, radius, alpha_c, beta_c;
+} gray_shadow_info;
+
+typedef struct gray_ctx gray_ctx; /* opaque */
+
+/* Fill *opt with the defaults named above (FP64, benchmark rule, 1e5 steps). */
+void gray_default_options(gray_options *opt);
+
+/* Bytes of device memory the state of n rays needs at this precision.
+ * Returns 0 for n < 0 or an unknown precision. */
+size_t gray_state_bytes(int64_t n, int32_t precision);
+
+/* Create a context: validates *opt, allocates the small device workspace
+ * (work-queue counters and statistics, < 4 KB) on the current device.
+ * Errors: GRAY_EINVAL (NULL pointer, bad option), GRAY_ENOMEM, GRAY_ECUDA. */
+int gray_create(gray_ctx **ctx, const gray_options *opt);
+
+/* Release the context and its workspace.  NULL is ignored. */
+void gray_destroy(gray_ctx *ctx);
+
+/* State buffers.  The state of n_state rays is one device buffer of
+ * gray_state_bytes(n_state, precision) bytes laid out as planes (structure of
+ * arrays) for exactly n_state rays; every call that touches it receives the
+ * same (state_dev, state_bytes, n_state), and calls that fill or read part of
+ * it say which rays with first_ray (and a count).  A buffer is tied to the
+ * precision of the context that set it up.  Calls fail with GRAY_EINVAL when
+ * state_bytes is smaller than gray_state_bytes(n_state, precision) or a ray
+ * range falls outside [0, n_state). */
+
+/* Image-plane initial conditions (the set-up the paper takes from Psaltis &
+ * Johannsen 2012, Sec. 2; plane at r_obs, Sec. 4), computed in double
+ * precision: writes the state of every pixel of n_images images, image after
+ * image, into rays first_ray, first_ray + 1, ... of the buffer.  Every ray is
+ * left ACTIVE with zero steps.
+ * Errors: GRAY_EINVAL (bad image, n_images < 1, range outside the buffer),
+ * GRAY_ECUDA. */
+int gray_setup(gray_ctx *ctx, const gray_image *images_host, int32_t n_images,
+               void *state_dev, size_t state_bytes, int64_t n_state, int64_t first_ray,
+               void *stream);
+
+/* Per-ray initial conditions: rays_dev holds n rows of 5 doubles
+ * (alpha, beta, a, incl, r_obs), mass M common to all; written into rays
+ * first_ray .. first_ray + n - 1.  Each row is validated by the caller (same
+ * ranges as gray_image).  Errors: GRAY_EINVAL, GRAY_ECUDA. */
+int gray_setup_rays(gray_ctx *ctx, const double *rays_dev, int64_t n, double M,
+                    void *state_dev, size_t state_bytes, int64_t n_state, int64_t first_ray,
+                    void *stream);
+
+/* Trace every ACTIVE ray of the buffer backward until it is captured,
+ * escapes, hits max_steps, turns non-finite, or has taken step_budget steps in
+ * this call (step_budget <= 0: no per-call budget; Sec. 2 notes the same
+ * step-limited mode for interactive use).  Finished rays are skipped, so a
+ * trace split over several calls gives the same result as one call.  If
+ * n_active_host is not NULL the call waits for the stream and stores the
+ * number of rays still active; if stats_host is not NULL (4 int64) it stores,
+ * for this call: steps taken, Euler redos, steps promoted to double, rays
+ * still active.  Returns 0 when no ray is active, 1 when some remain or when
+ * no host output was requested (the count is then unknown), or an error
+ * (GRAY_EINVAL, GRAY_ECUDA). */
+int gray_trace(gray_ctx *ctx, void *state_dev, size_t state_bytes, int64_t n_state,
+               int64_t step_budget, int64_t *n_active_host, int64_t *stats_host, void *stream);
+
+/* Read rays first_ray .. first_ray + n - 1 of the buffer into out_dev
+ * (out_bytes bytes):
+ *   GRAY_RENDER_PIXELS64    n gray_pixel64
+ *   GRAY_RENDER_PIXELS32    n gray_pixel32
+ *   GRAY_RENDER_RECORD      n x 17 doubles: status, steps, Euler redos, pole
+ *                           remaps, final (t, r, theta, phi) on the stop
+ *                           surface, state y[8] at the end of the last step
+ *                           (compensated value for FP32 modes), steps
+ *                           promoted to double
+ *   GRAY_RENDER_INVARIANTS  n x 4 doubles (E, L_z, Carter Q, g k k) of the
+ *                           stored state, evaluated in double
+ * Errors: GRAY_EINVAL (unknown kind, buffer too small, bad range), GRAY_ECUDA. */
+int gray_render(gray_ctx *ctx, const void *state_dev, size_t state_bytes, int64_t n_state,
+                int64_t first_ray, int64_t n, int32_t kind, void *out_dev, size_t out_bytes,
+                void *stream);
+
+/* Shadow of each of n_images images whose rays start at first_ray (as laid
+ * down by gray_setup with the same image list): captured count, area of the
+ * captured pixels on the image plane, equivalent radius sqrt(area/pi) and
+ * centroid (the quantities from which Sec. 4 builds its ring metrics).
+ * out_dev receives n_images gray_shadow_info records (out_bytes bytes).
+ * Errors: GRAY_EINVAL, GRAY_ECUDA. */
+int gray_shadow(gray_ctx *ctx, const void *state_dev, size_t state_bytes, int64_t n_state,
+                int64_t first_ray, const gray_image *images_host, int32_t n_images,
+                gray_shadow_info *out_dev, size_t out_bytes, void *stream);
+
+/* Evaluate one device function of the tracer on n inputs, in the arithmetic
+ * of `precision` (GRAY_FP64 or GRAY_FP32), for unit parity tests: in_dev and
+ * out_dev are n rows of doubles laid out as listed at GRAY_EVAL_*.
+ * Errors: GRAY_EINVAL, GRAY_ECUDA. */
+int gray_eval(int32_t what, int32_t precision, const double *in_dev, int64_t n,
+              double *out_dev, void *stream);
+
+/* Human-readable text of a return code; never NULL. */
+const char *gray_strerror(int code);
+
+/* Number of kernel launches made by this process through the library so far
+ * (diagnostic counter). */
+int64_t gray_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRAY_H */

@@ -1,0 +1,1132 @@
+// gray.cu -- kernels and C ABI of libgray (declared in include/gray.h).
+//
+// Kernels:
+//   setup_images_kernel / setup_rays_kernel  image-plane initial conditions (double)
+//   trace_kernel<MODE>                       persistent backward RK4 tracer
+//   render_kernel, shadow_*_kernel           read-out of results
+//   eval_kernel<T>                           unit evaluations for parity tests
+//
+// Trace kernel design (GRay Sec. 2 puts one photon in one thread; here a
+// warp owns 32 photons at a time and keeps each photon's state in registers):
+//   * a persistent grid (blocks_per_sm x SMs blocks) drains a global work
+//     queue of ray indices with one atomicAdd per warp refill;
+//   * every `refill` steps the warp ballots its idle lanes (rays that
+//     finished) and hands them new rays, so warps do not idle while a few
+//     long rays (near-critical orbits) run on;
+//   * rays are loaded and stored with 16-byte vector accesses from a
+//     structure-of-arrays state (one plane per 4-vector);
+//   * per-call statistics are reduced in the warp and added once per warp.
+// There is no spin-wait anywhere: a warp leaves when the queue is empty and
+// its lanes are idle, so every launch ends.
+#include "gray.h"
+#include "kerr.cuh"
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace gray;
+
+namespace {
+
+std::atomic<int64_t> g_launches{0};
+
+struct alignas(32) d4 {
+    double x, y, z, w;
+};
+
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Structure-of-arrays layout of the state of n rays (all planes 256-byte aligned):
+//   X  position (t, r, theta, phi)      float4 (FP32 modes) / d4 (FP64)
+//   K  momentum (k^t, k^r, k^th, k^ph)  float4 / d4
+//   CX, CK  Kahan compensations         float4 (FP32 modes only)
+//   F  final position on the stop surface  float4 / d4
+//   P  per-ray constants (a, M, r_obs, 0)  d4
+//   S0 (status, steps, Euler redos, pole remaps)  int4
+//   S1 steps promoted to double         int
+struct Layout {
+    size_t X, K, CX, CK, F, P, S0, S1, total;
+};
+
+inline bool is_f64(int prec) { return prec == GRAY_FP64; }
+
+Layout make_layout(int64_t n, int prec)
+{
+    Layout L{};
+    size_t off = 0;
+    const size_t un = (size_t)n;
+    const size_t v = is_f64(prec) ? 32 : 16;
+    L.X = off;
+    off = align256(off + v * un);
+    L.K = off;
+    off = align256(off + v * un);
+    if (!is_f64(prec)) {
+        L.CX = off;
+        off = align256(off + 16 * un);
+        L.CK = off;
+        off = align256(off + 16 * un);
+    } else {
+        L.CX = L.CK = 0;
+    }
+    L.F = off;
+    off = align256(off + v * un);
+    L.P = off;
+    off = align256(off + 32 * un);
+    L.S0 = off;
+    off = align256(off + 16 * un);
+    L.S1 = off;
+    off = align256(off + 4 * un);
+    L.total = off;
+    return L;
+}
+
+struct StateView {
+    char *X, *K, *CX, *CK, *F;
+    d4 *P;
+    int4 *S0;
+    int *S1;
+};
+
+StateView make_view(void *base, int64_t n, int prec)
+{
+    Layout L = make_layout(n, prec);
+    char *b = (char *)base;
+    StateView v;
+    v.X = b + L.X;
+    v.K = b + L.K;
+    v.CX = is_f64(prec) ? nullptr : b + L.CX;
+    v.CK = is_f64(prec) ? nullptr : b + L.CK;
+    v.F = b + L.F;
+    v.P = (d4 *)(b + L.P);
+    v.S0 = (int4 *)(b + L.S0);
+    v.S1 = (int *)(b + L.S1);
+    return v;
+}
+
+__device__ __forceinline__ d4 ld_d4(const void *p, int64_t i)
+{
+    const double2 *q = (const double2 *)p + 2 * i;
+    double2 a = q[0], b = q[1];
+    return d4{a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void st_d4(void *p, int64_t i, double x, double y, double z, double w)
+{
+    double2 *q = (double2 *)p + 2 * i;
+    q[0] = make_double2(x, y);
+    q[1] = make_double2(z, w);
+}
+__device__ __forceinline__ float4 ld_f4(const void *p, int64_t i) { return ((const float4 *)p)[i]; }
+__device__ __forceinline__ void st_f4(void *p, int64_t i, float x, float y, float z, float w)
+{
+    ((float4 *)p)[i] = make_float4(x, y, z, w);
+}
+
+// Workspace of one context (device memory, zeroed before each trace).
+struct Workspace {
+    unsigned long long head;   // next ray index handed out by the queue
+    unsigned long long steps;  // steps taken in this call
+    unsigned long long euler;  // Euler redos in this call
+    unsigned long long fp64;   // steps promoted to double in this call
+    unsigned long long active; // rays left active by this call
+    unsigned long long pad[3];
+};
+
+} // namespace
+
+struct gray_ctx {
+    gray_options opt;
+    Workspace *ws = nullptr;      // device
+    Workspace *ws_host = nullptr; // pinned host mirror
+    int device = 0;
+    int num_sms = 0;
+};
+
+namespace {
+
+// --------------------------------------------------------------------------
+// Set-up
+// --------------------------------------------------------------------------
+
+struct ImageDev {
+    double a, M, r_obs, incl, a0, da, b0, db;
+    long long first; // first ray of the image relative to the call's first ray
+    int nx, ny;
+};
+
+// Store one initial state (double) into the layout of `prec`.  FP32 modes keep
+// the rounding error of each component in the compensation plane, so a
+// compensated trace starts from the double-precision initial condition.
+__device__ void store_initial(const StateView &v, int prec, int64_t i, const double *y, double a, double M,
+                              double r_obs)
+{
+    if (prec == GRAY_FP64) {
+        st_d4(v.X, i, y[0], y[1], y[2], y[3]);
+        st_d4(v.K, i, y[4], y[5], y[6], y[7]);
+        st_d4(v.F, i, y[0], y[1], y[2], y[3]);
+    } else {
+        float hi[8], lo[8];
+        for (int m = 0; m < 8; ++m) {
+            hi[m] = (float)y[m];
+            lo[m] = (prec == GRAY_FP32) ? 0.0f : (float)((double)hi[m] - y[m]);
+        }
+        st_f4(v.X, i, hi[0], hi[1], hi[2], hi[3]);
+        st_f4(v.K, i, hi[4], hi[5], hi[6], hi[7]);
+        st_f4(v.CX, i, lo[0], lo[1], lo[2], lo[3]);
+        st_f4(v.CK, i, lo[4], lo[5], lo[6], lo[7]);
+        st_f4(v.F, i, hi[0], hi[1], hi[2], hi[3]);
+    }
+    st_d4(v.P, i, a, M, r_obs, 0.0);
+    v.S0[i] = make_int4(GRAY_RAY_ACTIVE, 0, 0, 0);
+    v.S1[i] = 0;
+}
+
+__global__ void setup_images_kernel(const ImageDev *imgs, int n_images, int64_t total, int64_t first_ray,
+                                    StateView v, int prec)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total)
+        return;
+    int lo = 0, hi = n_images - 1;
+    while (lo < hi) { // last image with first <= i
+        int mid = (lo + hi + 1) >> 1;
+        if (imgs[mid].first <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const ImageDev im = imgs[lo];
+    const int64_t p = i - im.first;
+    const int64_t row = p / im.nx, col = p - row * im.nx;
+    const double alpha = im.a0 + ((double)col + 0.5) * im.da;
+    const double beta = im.b0 + ((double)row + 0.5) * im.db;
+    double y[8];
+    initial_state(im.M, im.a, im.r_obs, im.incl, alpha, beta, y);
+    store_initial(v, prec, first_ray + i, y, im.a, im.M, im.r_obs);
+}
+
+__global__ void setup_rays_kernel(const double *rays, int64_t n, double M, int64_t first_ray, StateView v, int prec)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const double *q = rays + 5 * i;
+    double y[8];
+    initial_state(M, q[2], q[4], q[3], q[0], q[1], y);
+    store_initial(v, prec, first_ray + i, y, q[2], M, q[4]);
+}
+
+// --------------------------------------------------------------------------
+// One integration step (GRay Sec. 2 order): step size -> RK4 -> Eq. 4
+// monitor, Euler redo at h/9 on failure -> finite check -> stop tests with
+// the final point on the stop surface -> Eq. 3 remap.
+// --------------------------------------------------------------------------
+
+// State update y1 = y + inc, plain or compensated (Kahan: the true value is
+// y - c).
+template <typename T, bool KAHAN>
+__device__ __forceinline__ void add_update(const T *y, const T *c, const T *inc, T *y1, T *c1)
+{
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        if (KAHAN) {
+            const T d = inc[m] - c[m];
+            const T t = y[m] + d;
+            c1[m] = (t - y[m]) - d;
+            y1[m] = t;
+        } else {
+            y1[m] = y[m] + inc[m];
+        }
+    }
+}
+
+// Eq. 3 on the state; with compensation the new theta and phi are formed in
+// double from hi - lo so that the remap itself adds no rounding.
+template <typename T, bool KAHAN> __device__ __forceinline__ int remap_eq3(T *y, T *c)
+{
+    const T pi = pi_v<T>();
+    if (!(y[2] > pi) && !(y[2] < T(0)))
+        return 0;
+    const bool over = y[2] > pi;
+    if (KAHAN) {
+        const double th = (double)y[2] - (double)c[2];
+        const double ph = (double)y[3] - (double)c[3];
+        const double th2 = over ? 2.0 * 3.14159265358979323846 - th : -th;
+        const double ph2 = over ? ph + 3.14159265358979323846 : ph - 3.14159265358979323846;
+        y[2] = (T)th2;
+        c[2] = (T)((double)y[2] - th2);
+        y[3] = (T)ph2;
+        c[3] = (T)((double)y[3] - ph2);
+        y[6] = -y[6];
+        c[6] = -c[6];
+    } else {
+        if (over) {
+            y[2] = T(2) * pi - y[2];
+            y[3] = y[3] + pi;
+        } else {
+            y[2] = -y[2];
+            y[3] = y[3] - pi;
+        }
+        y[6] = -y[6];
+    }
+    return 1;
+}
+
+// One step.  Returns the ray's new status; writes fin[4] when it stops.
+template <typename T, bool KAHAN>
+__device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, T *y, T *c, T *fin, int &euler,
+                                         int &remaps)
+{
+    T h = step_size(H, O, y);
+    T a1[4], a2[4], a3[4], a4[4];
+    geodesic_accel(H, y[1], y[2], y[4], y[5], y[6], y[7], a1);
+    const T hh = T(0.5) * h;
+    const T r2 = fma(hh, y[5], y[1]), th2 = fma(hh, y[6], y[2]);
+    const T kt2 = fma(hh, a1[0], y[4]), kr2 = fma(hh, a1[1], y[5]), kh2 = fma(hh, a1[2], y[6]),
+            kp2 = fma(hh, a1[3], y[7]);
+    geodesic_accel(H, r2, th2, kt2, kr2, kh2, kp2, a2);
+    const T r3 = fma(hh, kr2, y[1]), th3 = fma(hh, kh2, y[2]);
+    const T kt3 = fma(hh, a2[0], y[4]), kr3 = fma(hh, a2[1], y[5]), kh3 = fma(hh, a2[2], y[6]),
+            kp3 = fma(hh, a2[3], y[7]);
+    geodesic_accel(H, r3, th3, kt3, kr3, kh3, kp3, a3);
+    const T r4 = fma(h, kr3, y[1]), th4 = fma(h, kh3, y[2]);
+    const T kt4 = fma(h, a3[0], y[4]), kr4 = fma(h, a3[1], y[5]), kh4 = fma(h, a3[2], y[6]),
+            kp4 = fma(h, a3[3], y[7]);
+    geodesic_accel(H, r4, th4, kt4, kr4, kh4, kp4, a4);
+    const T h6 = h / T(6);
+    T inc[8];
+    inc[0] = h6 * (y[4] + T(2) * (kt2 + kt3) + kt4);
+    inc[1] = h6 * (y[5] + T(2) * (kr2 + kr3) + kr4);
+    inc[2] = h6 * (y[6] + T(2) * (kh2 + kh3) + kh4);
+    inc[3] = h6 * (y[7] + T(2) * (kp2 + kp3) + kp4);
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        inc[4 + m] = h6 * (a1[m] + T(2) * (a2[m] + a3[m]) + a4[m]);
+    T y1[8], c1[8];
+    add_update<T, KAHAN>(y, c, inc, y1, c1);
+
+    // Eq. 4 monitor: redo the step as forward Euler at h/9 when |xi + 1| > eps.
+    const T xi = xi_eq4(H, y1);
+    if (!(fabs(xi + T(1)) <= O.eps_xi)) {
+        h = h / T(9);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            inc[m] = h * y[4 + m];
+            inc[4 + m] = h * a1[m];
+        }
+        add_update<T, KAHAN>(y, c, inc, y1, c1);
+        ++euler;
+    }
+
+    int status = GRAY_RAY_ACTIVE;
+    bool finite = true;
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+        finite &= isfinite(y1[m]);
+    if (!finite) {
+        status = GRAY_RAY_NONFINITE;
+        for (int m = 0; m < 4; ++m)
+            fin[m] = y1[m];
+    } else if (y1[1] <= H.r_cap) {
+        stop_surface(y, y1, h, H.r_cap, fin);
+        status = GRAY_RAY_CAPTURED;
+    } else if (y1[1] >= H.r_esc && h * y1[5] > T(0)) {
+        stop_surface(y, y1, h, H.r_esc, fin);
+        status = GRAY_RAY_ESCAPED;
+    }
+    if (status != GRAY_RAY_NONFINITE)
+        remaps += remap_eq3<T, KAHAN>(y1, c1);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        y[m] = y1[m];
+        if (KAHAN)
+            c[m] = c1[m];
+    }
+    return status;
+}
+
+// --------------------------------------------------------------------------
+// Persistent trace kernel
+// --------------------------------------------------------------------------
+
+struct TraceArgs {
+    StateView v;
+    int64_t n;
+    int64_t budget; // per-call step budget per ray, <= 0: none
+    int max_steps;
+    int refill;
+    double h_frac, h_min, eps_xi, cap_frac, r_esc_frac, r_sw;
+    int step_rule;
+    Workspace *ws;
+};
+
+template <int MODE> struct ModeTraits {
+    using T = float;
+    static constexpr bool kahan = (MODE == GRAY_FP32_KAHAN || MODE == GRAY_FP32_KAHAN_SEL64);
+    static constexpr bool sel64 = (MODE == GRAY_FP32_KAHAN_SEL64);
+};
+template <> struct ModeTraits<GRAY_FP64> {
+    using T = double;
+    static constexpr bool kahan = false;
+    static constexpr bool sel64 = false;
+};
+
+// The double step used for promoted steps of the selective mode, kept out of
+// line so its registers do not enlarge the single-precision hot loop.
+__device__ __noinline__ int step_promoted(const Hole<double> *H, const StepOpt<double> *O, float *y, float *c,
+                                          float *fin, int *euler, int *remaps)
+{
+    double yd[8], cd[8], find[4];
+    for (int m = 0; m < 8; ++m) {
+        yd[m] = (double)y[m] - (double)c[m];
+        cd[m] = 0.0;
+    }
+    int e = *euler, rm = *remaps;
+    int st = step_once<double, false>(*H, *O, yd, cd, find, e, rm);
+    *euler = e;
+    *remaps = rm;
+    for (int m = 0; m < 8; ++m) {
+        y[m] = (float)yd[m];
+        c[m] = (float)((double)y[m] - yd[m]);
+    }
+    for (int m = 0; m < 4; ++m)
+        fin[m] = (float)find[m];
+    return st;
+}
+
+template <int MODE> __global__ void trace_kernel(TraceArgs A)
+{
+    using T = typename ModeTraits<MODE>::T;
+    constexpr bool KAHAN = ModeTraits<MODE>::kahan;
+    constexpr bool SEL64 = ModeTraits<MODE>::sel64;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const StateView &v = A.v;
+
+    StepOpt<T> O;
+    O.h_frac = (T)A.h_frac;
+    O.h_min = (T)A.h_min;
+    O.eps_xi = (T)A.eps_xi;
+    O.step_rule = A.step_rule;
+    StepOpt<double> O64;
+    O64.h_frac = A.h_frac;
+    O64.h_min = A.h_min;
+    O64.eps_xi = A.eps_xi;
+    O64.step_rule = A.step_rule;
+
+    bool has = false;
+    bool exhausted = false;
+    int64_t id = 0;
+    T y[8], c[8], fin[4];
+    Hole<T> H;
+    Hole<double> H64;
+    int steps = 0, euler = 0, remaps = 0, n64 = 0;
+    int64_t call_steps = 0;
+    unsigned long long tot_steps = 0, tot_euler = 0, tot_fp64 = 0, tot_active = 0;
+
+    for (;;) {
+        // ---- refill idle lanes from the work queue (warp-uniform loop) ----
+        while (!exhausted) {
+            const unsigned idle = __ballot_sync(FULL, !has);
+            if (idle == 0)
+                break;
+            const int cnt = __popc(idle);
+            const int leader = __ffs(idle) - 1;
+            unsigned long long base = 0;
+            if (lane == leader)
+                base = atomicAdd(&A.ws->head, (unsigned long long)cnt);
+            base = __shfl_sync(FULL, base, leader);
+            if (!has) {
+                const int rank = __popc(idle & ((1u << lane) - 1u));
+                const int64_t my = (int64_t)base + rank;
+                if (my < A.n) {
+                    const int4 s0 = v.S0[my];
+                    if (s0.x == GRAY_RAY_ACTIVE) {
+                        has = true;
+                        id = my;
+                        steps = s0.y;
+                        euler = s0.z;
+                        remaps = s0.w;
+                        n64 = v.S1[my];
+                        call_steps = 0;
+                        const d4 p = ld_d4(v.P, my);
+                        H64 = make_hole(p.x, p.y, p.z, A.cap_frac, A.r_esc_frac, A.r_sw);
+                        H = cast_hole<T>(H64);
+                        if (MODE == GRAY_FP64) {
+                            const d4 X = ld_d4(v.X, my), K = ld_d4(v.K, my);
+                            y[0] = (T)X.x; y[1] = (T)X.y; y[2] = (T)X.z; y[3] = (T)X.w;
+                            y[4] = (T)K.x; y[5] = (T)K.y; y[6] = (T)K.z; y[7] = (T)K.w;
+                        } else {
+                            const float4 X = ld_f4(v.X, my), K = ld_f4(v.K, my);
+                            y[0] = (T)X.x; y[1] = (T)X.y; y[2] = (T)X.z; y[3] = (T)X.w;
+                            y[4] = (T)K.x; y[5] = (T)K.y; y[6] = (T)K.z; y[7] = (T)K.w;
+                            if (KAHAN) {
+                                const float4 CX = ld_f4(v.CX, my), CK = ld_f4(v.CK, my);
+                                c[0] = CX.x; c[1] = CX.y; c[2] = CX.z; c[3] = CX.w;
+                                c[4] = CK.x; c[5] = CK.y; c[6] = CK.z; c[7] = CK.w;
+                            }
+                        }
+                        if (!KAHAN)
+                            for (int m = 0; m < 8; ++m)
+                                c[m] = T(0);
+                    }
+                }
+            }
+            if ((int64_t)base + cnt >= A.n)
+                exhausted = true;
+        }
+        if (!__any_sync(FULL, has))
+            break;
+
+        // ---- step block: `refill` steps, then look for idle lanes again ----
+        for (int k = 0; k < A.refill; ++k) {
+            if (has) {
+                int status = GRAY_RAY_ACTIVE;
+                bool yield = false;
+                if (steps >= A.max_steps) {
+                    status = GRAY_RAY_STEP_CAP;
+                    for (int m = 0; m < 4; ++m)
+                        fin[m] = y[m];
+                } else if (A.budget > 0 && call_steps >= A.budget) {
+                    yield = true;
+                } else {
+                    const int e0 = euler;
+                    bool promoted = false;
+                    if constexpr (SEL64) {
+                        if ((double)y[1] - (double)c[1] < H64.r_promote) {
+                            status = step_promoted(&H64, &O64, y, c, fin, &euler, &remaps);
+                            promoted = true;
+                            ++n64;
+                            ++tot_fp64;
+                        }
+                    }
+                    if (!promoted)
+                        status = step_once<T, KAHAN>(H, O, y, c, fin, euler, remaps);
+                    tot_euler += (unsigned long long)(euler - e0);
+                    ++steps;
+                    ++call_steps;
+                    ++tot_steps;
+                }
+                if (status != GRAY_RAY_ACTIVE || yield) {
+                    // write the ray back
+                    if (MODE == GRAY_FP64) {
+                        st_d4(v.X, id, y[0], y[1], y[2], y[3]);
+                        st_d4(v.K, id, y[4], y[5], y[6], y[7]);
+                        if (status != GRAY_RAY_ACTIVE)
+                            st_d4(v.F, id, fin[0], fin[1], fin[2], fin[3]);
+                    } else {
+                        st_f4(v.X, id, (float)y[0], (float)y[1], (float)y[2], (float)y[3]);
+                        st_f4(v.K, id, (float)y[4], (float)y[5], (float)y[6], (float)y[7]);
+                        if (KAHAN) {
+                            st_f4(v.CX, id, (float)c[0], (float)c[1], (float)c[2], (float)c[3]);
+                            st_f4(v.CK, id, (float)c[4], (float)c[5], (float)c[6], (float)c[7]);
+                        }
+                        if (status != GRAY_RAY_ACTIVE)
+                            st_f4(v.F, id, (float)fin[0], (float)fin[1], (float)fin[2], (float)fin[3]);
+                    }
+                    v.S0[id] = make_int4(status, steps, euler, remaps);
+                    v.S1[id] = n64;
+                    if (yield)
+                        ++tot_active;
+                    has = false;
+                }
+            }
+        }
+    }
+
+    // ---- per-call statistics: one atomic per warp per counter ----
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        tot_steps += __shfl_xor_sync(FULL, tot_steps, off);
+        tot_euler += __shfl_xor_sync(FULL, tot_euler, off);
+        tot_fp64 += __shfl_xor_sync(FULL, tot_fp64, off);
+        tot_active += __shfl_xor_sync(FULL, tot_active, off);
+    }
+    if (lane == 0) {
+        if (tot_steps)
+            atomicAdd(&A.ws->steps, tot_steps);
+        if (tot_euler)
+            atomicAdd(&A.ws->euler, tot_euler);
+        if (tot_fp64)
+            atomicAdd(&A.ws->fp64, tot_fp64);
+        if (tot_active)
+            atomicAdd(&A.ws->active, tot_active);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Read-out
+// --------------------------------------------------------------------------
+
+__device__ void load_state_double(const StateView &v, int prec, int64_t i, double *y, double *fin)
+{
+    if (prec == GRAY_FP64) {
+        const d4 X = ld_d4(v.X, i), K = ld_d4(v.K, i), F = ld_d4(v.F, i);
+        y[0] = X.x; y[1] = X.y; y[2] = X.z; y[3] = X.w;
+        y[4] = K.x; y[5] = K.y; y[6] = K.z; y[7] = K.w;
+        fin[0] = F.x; fin[1] = F.y; fin[2] = F.z; fin[3] = F.w;
+    } else {
+        const float4 X = ld_f4(v.X, i), K = ld_f4(v.K, i), F = ld_f4(v.F, i);
+        float4 CX = make_float4(0, 0, 0, 0), CK = CX;
+        if (prec != GRAY_FP32) {
+            CX = ld_f4(v.CX, i);
+            CK = ld_f4(v.CK, i);
+        }
+        y[0] = (double)X.x - CX.x; y[1] = (double)X.y - CX.y; y[2] = (double)X.z - CX.z; y[3] = (double)X.w - CX.w;
+        y[4] = (double)K.x - CK.x; y[5] = (double)K.y - CK.y; y[6] = (double)K.z - CK.z; y[7] = (double)K.w - CK.w;
+        fin[0] = F.x; fin[1] = F.y; fin[2] = F.z; fin[3] = F.w;
+    }
+}
+
+__global__ void render_kernel(StateView v, int prec, int64_t first, int64_t n, int kind, void *out)
+{
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n)
+        return;
+    const int64_t i = first + j;
+    double y[8], fin[4];
+    load_state_double(v, prec, i, y, fin);
+    const int4 s0 = v.S0[i];
+    if (kind == GRAY_RENDER_PIXELS64) {
+        gray_pixel64 px;
+        px.r = fin[1];
+        px.theta = fin[2];
+        px.phi = fin[3];
+        px.status = s0.x;
+        px.steps = s0.y;
+        ((gray_pixel64 *)out)[j] = px;
+    } else if (kind == GRAY_RENDER_PIXELS32) {
+        gray_pixel32 px;
+        px.r = (float)fin[1];
+        px.theta = (float)fin[2];
+        px.phi = (float)fin[3];
+        px.status = s0.x;
+        ((gray_pixel32 *)out)[j] = px;
+    } else if (kind == GRAY_RENDER_RECORD) {
+        double *o = (double *)out + 17 * j;
+        o[0] = s0.x;
+        o[1] = s0.y;
+        o[2] = s0.z;
+        o[3] = s0.w;
+        for (int m = 0; m < 4; ++m)
+            o[4 + m] = fin[m];
+        for (int m = 0; m < 8; ++m)
+            o[8 + m] = y[m];
+        o[16] = v.S1[i];
+    } else { // GRAY_RENDER_INVARIANTS, in double from the stored state
+        const d4 p = ld_d4(v.P, i);
+        const Hole<double> H = make_hole(p.x, p.y, p.z, 1.0, 1.0, 0.0);
+        double s, c;
+        sincos(y[2], &s, &c);
+        const MetricPieces<double> m = metric_pieces(H, y[1], s, c);
+        const double kt = y[4], kr = y[5], kh = y[6], kp = y[7];
+        const double E = -(m.gtt * kt + m.gtp * kp);
+        const double L = m.gtp * kt + m.gpp * kp;
+        const double kth_low = m.gthth * kh;
+        const double Q = kth_low * kth_low + c * c * (-H.a * H.a * E * E + L * L / (s * s));
+        const double N = m.gtt * kt * kt + 2.0 * m.gtp * kt * kp + m.grr * kr * kr + m.gthth * kh * kh + m.gpp * kp * kp;
+        double *o = (double *)out + 4 * j;
+        o[0] = E;
+        o[1] = L;
+        o[2] = Q;
+        o[3] = N;
+    }
+}
+
+// Shadow moments: counts and sum of (alpha, beta) of captured pixels per image,
+// accumulated directly in the caller's output records, then finalised.
+__global__ void shadow_accum_kernel(StateView v, int64_t first, const ImageDev *imgs, int n_images, int64_t total,
+                                    gray_shadow_info *out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total)
+        return;
+    int lo = 0, hi = n_images - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (imgs[mid].first <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const ImageDev im = imgs[lo];
+    const int64_t p = i - im.first;
+    const int64_t row = p / im.nx, col = p - row * im.nx;
+    const int st = v.S0[first + i].x;
+    gray_shadow_info *o = out + lo;
+    if (st == GRAY_RAY_CAPTURED) {
+        atomicAdd((unsigned long long *)&o->n_captured, 1ull);
+        atomicAdd(&o->alpha_c, im.a0 + ((double)col + 0.5) * im.da);
+        atomicAdd(&o->beta_c, im.b0 + ((double)row + 0.5) * im.db);
+    } else if (st == GRAY_RAY_ESCAPED) {
+        atomicAdd((unsigned long long *)&o->n_escaped, 1ull);
+    } else {
+        atomicAdd((unsigned long long *)&o->n_other, 1ull);
+    }
+}
+
+__global__ void shadow_final_kernel(const ImageDev *imgs, int n_images, gray_shadow_info *out)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_images)
+        return;
+    gray_shadow_info s = out[k];
+    const double cell = fabs(imgs[k].da * imgs[k].db);
+    s.area = (double)s.n_captured * cell;
+    s.radius = sqrt(s.area / 3.14159265358979323846);
+    if (s.n_captured > 0) {
+        s.alpha_c /= (double)s.n_captured;
+        s.beta_c /= (double)s.n_captured;
+    }
+    out[k] = s;
+}
+
+// --------------------------------------------------------------------------
+// Unit evaluations for parity tests
+// --------------------------------------------------------------------------
+
+template <typename T> __global__ void eval_kernel(int what, const double *in, int64_t n, double *out)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    if (what == GRAY_EVAL_CHRISTOFFEL) {
+        const double *q = in + 4 * i;
+        const Hole<T> H = cast_hole<T>(make_hole(q[1], q[0], 1.0, 1.0, 1.0, 0.0));
+        T G[64];
+        christoffel_closed_form<T>(H, (T)q[2], (T)q[3], G);
+        for (int m = 0; m < 64; ++m)
+            out[64 * i + m] = (double)G[m];
+    } else if (what == GRAY_EVAL_RHS) {
+        const double *q = in + 10 * i;
+        const Hole<T> H = cast_hole<T>(make_hole(q[1], q[0], 1.0, 1.0, 1.0, 0.0));
+        T y[8];
+        for (int m = 0; m < 8; ++m)
+            y[m] = (T)q[2 + m];
+        T acc[4];
+        geodesic_accel<T>(H, y[1], y[2], y[4], y[5], y[6], y[7], acc);
+        for (int m = 0; m < 4; ++m) {
+            out[8 * i + m] = (double)y[4 + m];
+            out[8 * i + 4 + m] = (double)acc[m];
+        }
+    } else if (what == GRAY_EVAL_INITIAL) {
+        const double *q = in + 6 * i;
+        double y[8];
+        initial_state(q[0], q[1], q[2], q[3], q[4], q[5], y);
+        for (int m = 0; m < 8; ++m)
+            out[8 * i + m] = y[m];
+    } else if (what == GRAY_EVAL_XI) {
+        const double *q = in + 10 * i;
+        const Hole<T> H = cast_hole<T>(make_hole(q[1], q[0], 1.0, 1.0, 1.0, 0.0));
+        T y[8];
+        for (int m = 0; m < 8; ++m)
+            y[m] = (T)q[2 + m];
+        out[i] = (double)xi_eq4<T>(H, y);
+    }
+}
+
+// --------------------------------------------------------------------------
+// Host helpers
+// --------------------------------------------------------------------------
+
+int cuda_err(cudaError_t e) { return e == cudaSuccess ? GRAY_OK : GRAY_ECUDA; }
+
+int check_launch()
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return cuda_err(cudaGetLastError());
+}
+
+bool finite_all(std::initializer_list<double> xs)
+{
+    for (double x : xs)
+        if (!std::isfinite(x))
+            return false;
+    return true;
+}
+
+int validate_options(const gray_options *o)
+{
+    if (!o)
+        return GRAY_EINVAL;
+    if (o->precision < GRAY_FP64 || o->precision > GRAY_FP32_KAHAN_SEL64)
+        return GRAY_EINVAL;
+    if (o->step_rule != GRAY_STEP_BENCH && o->step_rule != GRAY_STEP_EQ2)
+        return GRAY_EINVAL;
+    if (o->max_steps < 1)
+        return GRAY_EINVAL;
+    if (o->block != 0 && (o->block < 32 || o->block > 1024 || o->block % 32 != 0))
+        return GRAY_EINVAL;
+    if (o->blocks_per_sm < 0 || o->blocks_per_sm > 64 || o->refill < 0 || o->refill > 100000)
+        return GRAY_EINVAL;
+    if (!finite_all({o->h_frac, o->h_min, o->cap_frac, o->eps_xi, o->r_esc_frac, o->r_sw}))
+        return GRAY_EINVAL;
+    if (!(o->h_frac > 0) || !(o->h_min > 0) || !(o->cap_frac >= 1.0) || !(o->eps_xi > 0) ||
+        !(o->r_esc_frac > 0) || !(o->r_sw >= 0))
+        return GRAY_EINVAL;
+    return GRAY_OK;
+}
+
+int validate_image(const gray_image &im)
+{
+    if (!finite_all({im.a, im.M, im.r_obs, im.incl, im.alpha0, im.alpha1, im.beta0, im.beta1}))
+        return GRAY_EINVAL;
+    if (!(im.M >= 0) || !(im.r_obs > 0) || im.nx < 1 || im.ny < 1)
+        return GRAY_EINVAL;
+    if (im.M > 0 && !(std::fabs(im.a) < im.M))
+        return GRAY_EINVAL;
+    if (im.incl < 0 || im.incl > 3.14159265358979323846)
+        return GRAY_EINVAL;
+    if (!(im.alpha1 != im.alpha0) || !(im.beta1 != im.beta0))
+        return GRAY_EINVAL;
+    return GRAY_OK;
+}
+
+int check_state(const gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_state)
+{
+    if (!ctx || !state || n_state < 0)
+        return GRAY_EINVAL;
+    if (state_bytes < gray_state_bytes(n_state, ctx->opt.precision))
+        return GRAY_EINVAL;
+    return GRAY_OK;
+}
+
+unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+std::vector<ImageDev> image_table(const gray_image *images, int n_images, int64_t &total)
+{
+    std::vector<ImageDev> t((size_t)n_images);
+    total = 0;
+    for (int k = 0; k < n_images; ++k) {
+        const gray_image &im = images[k];
+        ImageDev &d = t[(size_t)k];
+        d.a = im.a;
+        d.M = im.M;
+        d.r_obs = im.r_obs;
+        d.incl = im.incl;
+        d.a0 = im.alpha0;
+        d.da = (im.alpha1 - im.alpha0) / im.nx;
+        d.b0 = im.beta0;
+        d.db = (im.beta1 - im.beta0) / im.ny;
+        d.nx = im.nx;
+        d.ny = im.ny;
+        d.first = total;
+        total += (int64_t)im.nx * im.ny;
+    }
+    return t;
+}
+
+// Copy a small host table to the device on `stream` through a temporary
+// buffer that is freed after the stream reaches it.
+int upload_table(const void *host, size_t bytes, cudaStream_t s, void **dev)
+{
+    *dev = nullptr;
+    if (cudaMallocAsync(dev, bytes, s) != cudaSuccess)
+        return GRAY_ECUDA;
+    if (cudaMemcpyAsync(*dev, host, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return GRAY_ECUDA;
+    return GRAY_OK;
+}
+
+} // namespace
+
+// ==========================================================================
+// C ABI
+// ==========================================================================
+
+extern "C" {
+
+void gray_default_options(gray_options *o)
+{
+    if (!o)
+        return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = GRAY_FP64;
+    o->step_rule = GRAY_STEP_BENCH;
+    o->max_steps = 100000;
+    o->block = 0;
+    o->blocks_per_sm = 0;
+    o->refill = 0;
+    o->h_frac = 1.0 / 32.0;
+    o->h_min = 1e-3;
+    o->cap_frac = 1.01;
+    o->eps_xi = 1e-3;
+    o->r_esc_frac = 1.0;
+    o->r_sw = 0.0;
+}
+
+size_t gray_state_bytes(int64_t n, int32_t precision)
+{
+    if (n < 0 || precision < GRAY_FP64 || precision > GRAY_FP32_KAHAN_SEL64)
+        return 0;
+    return make_layout(n, precision).total;
+}
+
+int gray_create(gray_ctx **ctx, const gray_options *opt)
+{
+    if (!ctx)
+        return GRAY_EINVAL;
+    *ctx = nullptr;
+    int rc = validate_options(opt);
+    if (rc)
+        return rc;
+    gray_ctx *c = new (std::nothrow) gray_ctx;
+    if (!c)
+        return GRAY_ENOMEM;
+    c->opt = *opt;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        delete c;
+        return GRAY_ECUDA;
+    }
+    if (cudaMalloc((void **)&c->ws, sizeof(Workspace)) != cudaSuccess) {
+        delete c;
+        return GRAY_ENOMEM;
+    }
+    if (cudaMallocHost((void **)&c->ws_host, sizeof(Workspace)) != cudaSuccess) {
+        cudaFree(c->ws);
+        delete c;
+        return GRAY_ENOMEM;
+    }
+    std::memset(c->ws_host, 0, sizeof(Workspace));
+    *ctx = c;
+    return GRAY_OK;
+}
+
+void gray_destroy(gray_ctx *ctx)
+{
+    if (!ctx)
+        return;
+    cudaFree(ctx->ws);
+    cudaFreeHost(ctx->ws_host);
+    delete ctx;
+}
+
+int gray_setup(gray_ctx *ctx, const gray_image *images, int32_t n_images, void *state, size_t state_bytes,
+               int64_t n_state, int64_t first_ray, void *stream)
+{
+    int rc = check_state(ctx, state, state_bytes, n_state);
+    if (rc)
+        return rc;
+    if (!images || n_images < 1 || first_ray < 0)
+        return GRAY_EINVAL;
+    for (int k = 0; k < n_images; ++k)
+        if ((rc = validate_image(images[k])))
+            return rc;
+    int64_t total = 0;
+    std::vector<ImageDev> t = image_table(images, n_images, total);
+    if (first_ray + total > n_state)
+        return GRAY_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *dimg = nullptr;
+    if ((rc = upload_table(t.data(), t.size() * sizeof(ImageDev), s, &dimg)))
+        return rc;
+    StateView v = make_view(state, n_state, ctx->opt.precision);
+    setup_images_kernel<<<grid_for(total, 256), 256, 0, s>>>((const ImageDev *)dimg, n_images, total, first_ray, v,
+                                                           ctx->opt.precision);
+    rc = check_launch();
+    cudaError_t e = cudaFreeAsync(dimg, s);
+    if (rc)
+        return rc;
+    return cuda_err(e);
+}
+
+int gray_setup_rays(gray_ctx *ctx, const double *rays, int64_t n, double M, void *state, size_t state_bytes,
+                    int64_t n_state, int64_t first_ray, void *stream)
+{
+    int rc = check_state(ctx, state, state_bytes, n_state);
+    if (rc)
+        return rc;
+    if (n < 0 || first_ray < 0 || first_ray + n > n_state || !std::isfinite(M) || M < 0)
+        return GRAY_EINVAL;
+    if (n == 0)
+        return GRAY_OK;
+    if (!rays)
+        return GRAY_EINVAL;
+    StateView v = make_view(state, n_state, ctx->opt.precision);
+    setup_rays_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(rays, n, M, first_ray, v,
+                                                                        ctx->opt.precision);
+    return check_launch();
+}
+
+int gray_trace(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, int64_t step_budget,
+               int64_t *n_active_host, int64_t *stats_host, void *stream)
+{
+    int rc = check_state(ctx, state, state_bytes, n_state);
+    if (rc)
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(ctx->ws, 0, sizeof(Workspace), s) != cudaSuccess)
+        return GRAY_ECUDA;
+    const gray_options &o = ctx->opt;
+    if (n_state > 0) {
+        TraceArgs A;
+        A.v = make_view(state, n_state, o.precision);
+        A.n = n_state;
+        A.budget = step_budget;
+        A.max_steps = o.max_steps;
+        A.refill = o.refill > 0 ? o.refill : 8;
+        A.h_frac = o.h_frac;
+        A.h_min = o.h_min;
+        A.eps_xi = o.eps_xi;
+        A.cap_frac = o.cap_frac;
+        A.r_esc_frac = o.r_esc_frac;
+        A.r_sw = o.r_sw;
+        A.step_rule = o.step_rule;
+        A.ws = ctx->ws;
+        const int block = o.block > 0 ? o.block : 128;
+        int per_sm = o.blocks_per_sm;
+        if (per_sm <= 0) {
+            per_sm = 1;
+            switch (o.precision) {
+            case GRAY_FP64:
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<GRAY_FP64>, block, 0);
+                break;
+            case GRAY_FP32:
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<GRAY_FP32>, block, 0);
+                break;
+            case GRAY_FP32_KAHAN:
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<GRAY_FP32_KAHAN>, block, 0);
+                break;
+            default:
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<GRAY_FP32_KAHAN_SEL64>, block,
+                                                              0);
+                break;
+            }
+            if (per_sm < 1)
+                per_sm = 1;
+        }
+        int64_t want = (int64_t)per_sm * ctx->num_sms;
+        const int64_t need = (n_state + block - 1) / block;
+        if (want > need)
+            want = need;
+        const unsigned grid = (unsigned)(want > 0 ? want : 1);
+        switch (o.precision) {
+        case GRAY_FP64:
+            trace_kernel<GRAY_FP64><<<grid, block, 0, s>>>(A);
+            break;
+        case GRAY_FP32:
+            trace_kernel<GRAY_FP32><<<grid, block, 0, s>>>(A);
+            break;
+        case GRAY_FP32_KAHAN:
+            trace_kernel<GRAY_FP32_KAHAN><<<grid, block, 0, s>>>(A);
+            break;
+        default:
+            trace_kernel<GRAY_FP32_KAHAN_SEL64><<<grid, block, 0, s>>>(A);
+            break;
+        }
+        if ((rc = check_launch()))
+            return rc;
+    }
+    if (!n_active_host && !stats_host)
+        return 1;
+    if (cudaMemcpyAsync(ctx->ws_host, ctx->ws, sizeof(Workspace), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return GRAY_ECUDA;
+    const Workspace &w = *ctx->ws_host;
+    if (n_active_host)
+        *n_active_host = (int64_t)w.active;
+    if (stats_host) {
+        stats_host[0] = (int64_t)w.steps;
+        stats_host[1] = (int64_t)w.euler;
+        stats_host[2] = (int64_t)w.fp64;
+        stats_host[3] = (int64_t)w.active;
+    }
+    return w.active ? 1 : 0;
+}
+
+int gray_render(gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_state, int64_t first_ray, int64_t n,
+                int32_t kind, void *out, size_t out_bytes, void *stream)
+{
+    int rc = check_state(ctx, state, state_bytes, n_state);
+    if (rc)
+        return rc;
+    if (n < 0 || first_ray < 0 || first_ray + n > n_state)
+        return GRAY_EINVAL;
+    size_t per;
+    switch (kind) {
+    case GRAY_RENDER_PIXELS64: per = sizeof(gray_pixel64); break;
+    case GRAY_RENDER_PIXELS32: per = sizeof(gray_pixel32); break;
+    case GRAY_RENDER_RECORD: per = 17 * sizeof(double); break;
+    case GRAY_RENDER_INVARIANTS: per = 4 * sizeof(double); break;
+    default: return GRAY_EINVAL;
+    }
+    if (n == 0)
+        return GRAY_OK;
+    if (!out || out_bytes < per * (size_t)n)
+        return GRAY_EINVAL;
+    StateView v = make_view((void *)state, n_state, ctx->opt.precision);
+    render_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(v, ctx->opt.precision, first_ray, n, kind, out);
+    return check_launch();
+}
+
+int gray_shadow(gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_state, int64_t first_ray,
+                const gray_image *images, int32_t n_images, gray_shadow_info *out, size_t out_bytes, void *stream)
+{
+    int rc = check_state(ctx, state, state_bytes, n_state);
+    if (rc)
+        return rc;
+    if (!images || n_images < 1 || first_ray < 0 || !out || out_bytes < sizeof(gray_shadow_info) * (size_t)n_images)
+        return GRAY_EINVAL;
+    int64_t total = 0;
+    std::vector<ImageDev> t = image_table(images, n_images, total);
+    if (first_ray + total > n_state)
+        return GRAY_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *dimg = nullptr;
+    if ((rc = upload_table(t.data(), t.size() * sizeof(ImageDev), s, &dimg)))
+        return rc;
+    if (cudaMemsetAsync(out, 0, sizeof(gray_shadow_info) * (size_t)n_images, s) != cudaSuccess)
+        return GRAY_ECUDA;
+    StateView v = make_view((void *)state, n_state, ctx->opt.precision);
+    shadow_accum_kernel<<<grid_for(total, 256), 256, 0, s>>>(v, first_ray, (const ImageDev *)dimg, n_images, total,
+                                                            out);
+    if ((rc = check_launch()))
+        return rc;
+    shadow_final_kernel<<<grid_for(n_images, 128), 128, 0, s>>>((const ImageDev *)dimg, n_images, out);
+    rc = check_launch();
+    cudaError_t e = cudaFreeAsync(dimg, s);
+    if (rc)
+        return rc;
+    return cuda_err(e);
+}
+
+int gray_eval(int32_t what, int32_t precision, const double *in, int64_t n, double *out, void *stream)
+{
+    if (what < GRAY_EVAL_CHRISTOFFEL || what > GRAY_EVAL_XI || n < 0)
+        return GRAY_EINVAL;
+    if (precision != GRAY_FP64 && precision != GRAY_FP32)
+        return GRAY_EINVAL;
+    if (n == 0)
+        return GRAY_OK;
+    if (!in || !out)
+        return GRAY_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == GRAY_FP64)
+        eval_kernel<double><<<grid_for(n, 128), 128, 0, s>>>(what, in, n, out);
+    else
+        eval_kernel<float><<<grid_for(n, 128), 128, 0, s>>>(what, in, n, out);
+    return check_launch();
+}
+
+const char *gray_strerror(int code)
+{
+    switch (code) {
+    case GRAY_OK: return "success";
+    case 1: return "rays remain active after the step budget";
+    case GRAY_EINVAL: return "invalid argument";
+    case GRAY_ECUDA: return "CUDA runtime error";
+    case GRAY_ENOMEM: return "out of memory";
+    default: return "unknown error code";
+    }
+}
+
+int64_t gray_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+} // extern "C"

@@ -1,0 +1,323 @@
+// kerr.cuh -- device arithmetic of the Kerr photon tracer, templated on the
+// floating-point type (float or double).
+//
+// Kerr metric in Boyer-Lindquist coordinates x = (t, r, theta, phi), units
+// G = c = 1, mass M, spin a:
+//   Sigma = r^2 + a^2 cos^2 th,   Delta = r^2 - 2 M r + a^2,
+//   g_tt = -(1 - 2 M r/Sigma), g_tph = -2 M a r sin^2 th / Sigma,
+//   g_rr = Sigma/Delta, g_thth = Sigma,
+//   g_phph = (r^2 + a^2 + 2 M a^2 r sin^2 th / Sigma) sin^2 th.
+// The geodesic equation d^2 x^mu/dl^2 = -Gamma^mu_ab k^a k^b (GRay, Sec. 2,
+// which takes it from Psaltis & Johannsen 2012) is integrated with RK4.
+//
+// The Christoffel symbols are used in closed form.  With s = sin th,
+// c = cos th, A = r^2 - a^2 c^2, P = r^2 + a^2, the twenty independent
+// nonzero symbols are (christoffel_closed_form below):
+//   G^t_tr  = M P A / (Sigma^2 Delta)       G^t_tth = -2 M a^2 r s c / Sigma^2
+//   G^t_rph = -M a s^2 (a^2 c^2 (r^2 - a^2) + r^2 (a^2 + 3 r^2)) / (Sigma^2 Delta)
+//   G^t_thph = 2 M a^3 r s^3 c / Sigma^2
+//   G^r_tt  = M Delta A / Sigma^3           G^r_tph = -M a Delta s^2 A / Sigma^3
+//   G^r_rr  = (a^2 r s^2 - M A) / (Sigma Delta)
+//   G^r_rth = -a^2 s c / Sigma              G^r_thth = -r Delta / Sigma
+//   G^r_phph = -Delta s^2 (r Sigma^2 - M a^2 s^2 A) / Sigma^3
+//   G^th_tt = -2 M a^2 r s c / Sigma^3      G^th_tph = 2 M a r P s c / Sigma^3
+//   G^th_rr = a^2 s c / (Sigma Delta)       G^th_rth = r / Sigma
+//   G^th_thth = -a^2 s c / Sigma
+//   G^th_phph = -s c (P Sigma^2 + 2 M a^2 r s^2 (Sigma + P)) / Sigma^3
+//   G^ph_tr = M a A / (Sigma^2 Delta)       G^ph_tth = -2 M a r cot th / Sigma^2
+//   G^ph_rph = (r Sigma^2 + M (a^4 s^2 c^2 - r^2 (Sigma + P))) / (Sigma^2 Delta)
+//   G^ph_thph = cot th (Sigma^2 + 2 M a^2 r s^2) / Sigma^2
+// The right-hand side contracts them with k k.  Grouping the terms with
+// w = k^t - a s^2 k^ph (and using P - a^2 s^2 = Sigma) gives the exact,
+// shorter form evaluated per RK4 stage in geodesic_accel.
+//
+// Delta is evaluated as (r - r_+)(r - r_-) + dc with the horizon roots r_+-
+// taken once per ray in double precision (dc = max(a^2 - M^2, 0) covers M = 0):
+// in single precision this keeps Delta's relative error at the rounding of r
+// itself near the horizon, where r^2 - 2 M r + a^2 cancels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace gray {
+
+__device__ __forceinline__ void fsincos(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ void fsincos(double x, double *s, double *c) { sincos(x, s, c); }
+template <typename T> __device__ __forceinline__ T pi_v();
+template <> __device__ __forceinline__ float pi_v<float>() { return 3.14159265358979323846f; }
+template <> __device__ __forceinline__ double pi_v<double>() { return 3.14159265358979323846; }
+
+// Per-ray constants of the spacetime and of the stop surfaces.
+template <typename T> struct Hole {
+    T a, M;
+    T rp, rm, dc; // Delta = (r - rp)(r - rm) + dc
+    T r_h;        // horizon used by the step guard; -inf when M = 0 (no guard)
+    T r_cap;      // capture radius cap_frac * r_h; -1 when M = 0 (no capture)
+    T r_esc;      // escape radius
+    T r_promote;  // FP32_KAHAN_SEL64: steps with r below this run in double
+};
+
+// Integration options used inside a step.
+template <typename T> struct StepOpt {
+    T h_frac, h_min, eps_xi;
+    int step_rule; // 0: benchmark rule, 1: Eq. 2
+};
+
+// Build the per-ray constants in double precision (one square root per ray).
+__host__ __device__ inline Hole<double> make_hole(double a, double M, double r_obs, double cap_frac,
+                                                  double r_esc_frac, double r_sw)
+{
+    Hole<double> H;
+    H.a = a;
+    H.M = M;
+    double disc = M * M - a * a;
+    double root = disc > 0.0 ? sqrt(disc) : 0.0;
+    H.rp = M + root;
+    H.rm = M - root;
+    H.dc = disc < 0.0 ? -disc : 0.0;
+    if (M > 0.0) {
+        H.r_h = H.rp;
+        H.r_cap = cap_frac * H.rp;
+        H.r_promote = H.r_cap + r_sw;
+    } else {
+        H.r_h = -INFINITY;
+        H.r_cap = -1.0;
+        H.r_promote = -INFINITY;
+    }
+    H.r_esc = r_esc_frac * r_obs;
+    return H;
+}
+
+template <typename T> __host__ __device__ inline Hole<T> cast_hole(const Hole<double> &h)
+{
+    Hole<T> o;
+    o.a = (T)h.a;
+    o.M = (T)h.M;
+    o.rp = (T)h.rp;
+    o.rm = (T)h.rm;
+    o.dc = (T)h.dc;
+    o.r_h = (T)h.r_h;
+    o.r_cap = (T)h.r_cap;
+    o.r_esc = (T)h.r_esc;
+    o.r_promote = (T)h.r_promote;
+    return o;
+}
+
+// Metric pieces at (r, theta) with sin/cos given.
+template <typename T> struct MetricPieces {
+    T s2, Sigma, Delta, gtt, gtp, grr, gthth, gpp;
+};
+
+template <typename T>
+__device__ __forceinline__ MetricPieces<T> metric_pieces(const Hole<T> &H, T r, T s, T c)
+{
+    MetricPieces<T> m;
+    T a2 = H.a * H.a;
+    m.s2 = s * s;
+    m.Sigma = fma(a2, c * c, r * r);
+    m.Delta = fma(r - H.rp, r - H.rm, H.dc);
+    T iS = T(1) / m.Sigma;
+    T twoMr = T(2) * H.M * r;
+    m.gtt = -(T(1) - twoMr * iS);
+    m.gtp = -twoMr * H.a * m.s2 * iS;
+    m.grr = m.Sigma / m.Delta;
+    m.gthth = m.Sigma;
+    m.gpp = (r * r + a2 + twoMr * a2 * m.s2 * iS) * m.s2;
+    return m;
+}
+
+// Eq. 4: xi = [g_rr (k^r)^2 + g_phph (k^ph)^2 + g_thth (k^th)^2
+//             + 2 g_tph k^t k^ph] / [g_tt (k^t)^2]; -1 on a null vector.
+template <typename T> __device__ __forceinline__ T xi_eq4(const Hole<T> &H, const T *y)
+{
+    T s, c;
+    fsincos(y[2], &s, &c);
+    MetricPieces<T> m = metric_pieces(H, y[1], s, c);
+    T kt = y[4], kr = y[5], kh = y[6], kp = y[7];
+    T num = m.grr * kr * kr + m.gpp * kp * kp + m.gthth * kh * kh + T(2) * m.gtp * kt * kp;
+    return num / (m.gtt * kt * kt);
+}
+
+// The twenty closed-form symbols, written into G[mu][a][b] (symmetric in a,b).
+template <typename T>
+__device__ inline void christoffel_closed_form(const Hole<T> &H, T r, T th, T *G)
+{
+    T s, c;
+    fsincos(th, &s, &c);
+    const T a = H.a, M = H.M;
+    const T a2 = a * a, r2 = r * r, s2 = s * s, c2 = c * c, sc = s * c;
+    const T Sigma = fma(a2, c2, r2);
+    const T Delta = fma(r - H.rp, r - H.rm, H.dc);
+    const T iS = T(1) / Sigma, iD = T(1) / Delta;
+    const T iS2 = iS * iS, iS3 = iS2 * iS;
+    const T A = fma(-a2, c2, r2), P = r2 + a2;
+    const T cot = c / s;
+    for (int i = 0; i < 64; ++i) G[i] = T(0);
+#define GSET(m, i, j, v)                                                                                         \
+    do {                                                                                                         \
+        T v_ = (v);                                                                                              \
+        G[(m) * 16 + (i) * 4 + (j)] = v_;                                                                        \
+        G[(m) * 16 + (j) * 4 + (i)] = v_;                                                                        \
+    } while (0)
+    GSET(0, 0, 1, M * P * A * iS2 * iD);
+    GSET(0, 0, 2, -T(2) * M * a2 * r * sc * iS2);
+    GSET(0, 1, 3, -M * a * s2 * (a2 * c2 * (r2 - a2) + r2 * (a2 + T(3) * r2)) * iS2 * iD);
+    GSET(0, 2, 3, T(2) * M * a2 * a * r * s2 * sc * iS2);
+    GSET(1, 0, 0, M * Delta * A * iS3);
+    GSET(1, 0, 3, -M * a * Delta * s2 * A * iS3);
+    GSET(1, 1, 1, (a2 * r * s2 - M * A) * iS * iD);
+    GSET(1, 1, 2, -a2 * sc * iS);
+    GSET(1, 2, 2, -r * Delta * iS);
+    GSET(1, 3, 3, -Delta * s2 * (r * Sigma * Sigma - M * a2 * s2 * A) * iS3);
+    GSET(2, 0, 0, -T(2) * M * a2 * r * sc * iS3);
+    GSET(2, 0, 3, T(2) * M * a * r * P * sc * iS3);
+    GSET(2, 1, 1, a2 * sc * iS * iD);
+    GSET(2, 1, 2, r * iS);
+    GSET(2, 2, 2, -a2 * sc * iS);
+    GSET(2, 3, 3, -sc * (P * Sigma * Sigma + T(2) * M * a2 * r * s2 * (Sigma + P)) * iS3);
+    GSET(3, 0, 1, M * a * A * iS2 * iD);
+    GSET(3, 0, 2, -T(2) * M * a * r * cot * iS2);
+    GSET(3, 1, 3, (r * Sigma * Sigma + M * (a2 * a2 * s2 * c2 - r2 * (Sigma + P))) * iS2 * iD);
+    GSET(3, 2, 3, cot * (Sigma * Sigma + T(2) * M * a2 * r * s2) * iS2);
+#undef GSET
+}
+
+// dk^mu/dl = -Gamma^mu_ab k^a k^b, from the closed-form symbols grouped with
+// w = k^t - a s^2 k^ph.  Inputs: r, theta and k = (kt, kr, kh, kp).
+template <typename T>
+__device__ __forceinline__ void geodesic_accel(const Hole<T> &H, T r, T th, T kt, T kr, T kh, T kp, T *acc)
+{
+    T s, c;
+    fsincos(th, &s, &c);
+    const T a = H.a, M = H.M;
+    const T a2 = a * a, r2 = r * r, s2 = s * s, c2 = c * c, sc = s * c;
+    const T Sigma = fma(a2, c2, r2);
+    const T Delta = fma(r - H.rp, r - H.rm, H.dc);
+    const T iS = T(1) / Sigma, iD = T(1) / Delta;
+    const T iS2 = iS * iS;
+    const T A = fma(-a2, c2, r2), P = r2 + a2;
+    const T w = fma(-a * s2, kp, kt);
+    const T cot = c / s;
+    const T Mr = M * r;
+    // t: -2 M/Sigma [ kr/Delta (P A w/Sigma - 2 a r^2 s^2 kp) - 2 a^2 r s c kh w/Sigma ]
+    const T u_t = fma(iS * P * A, w, -T(2) * a * r2 * s2 * kp);
+    acc[0] = -T(2) * M * iS * (iD * kr * u_t - T(2) * a2 * r * sc * iS * kh * w);
+    // r: [-M Delta A w^2/Sigma^2 + Delta r (s^2 kp^2 + kh^2)
+    //     - (a^2 r s^2 - M A) kr^2/Delta + 2 a^2 s c kr kh] / Sigma
+    const T ang = fma(s2 * kp, kp, kh * kh);
+    const T u_r = -M * Delta * A * iS2 * w * w + Delta * r * ang - (a2 * r * s2 - M * A) * iD * kr * kr
+                  + T(2) * a2 * sc * kr * kh;
+    acc[1] = iS * u_r;
+    // theta: { s c [2 M a^2 r w^2/Sigma^2 - 4 M a r w kp/Sigma + P kp^2
+    //          - a^2 kr^2/Delta + a^2 kh^2] - 2 r kr kh } / Sigma
+    const T u_h = T(2) * Mr * a2 * iS2 * w * w - T(4) * Mr * a * iS * w * kp + P * kp * kp - a2 * iD * kr * kr
+                  + a2 * kh * kh;
+    acc[2] = iS * (sc * u_h - T(2) * r * kr * kh);
+    // phi: -2 [ kr/Delta (r kp (1 - 2 M r/Sigma) + M a A w/Sigma^2)
+    //          + cot kh (kp - 2 M a r w/Sigma^2) ]
+    const T u_p1 = r * kp * (T(1) - T(2) * Mr * iS) + M * a * A * iS2 * w;
+    const T u_p2 = kp - T(2) * Mr * a * iS2 * w;
+    acc[3] = -T(2) * (kr * iD * u_p1 + cot * kh * u_p2);
+}
+
+// Step size (negative: backward trace).  Benchmark rule
+// |h| = max(min(h_frac r, (r - r_h)/(2|k^r|)), h_min), or Eq. 2
+// |h| = max(min(h_frac / (|k^r/r| + |k^th| + |k^ph|), (r - r_h)/(2|k^r|)), h_min).
+template <typename T> __device__ __forceinline__ T step_size(const Hole<T> &H, const StepOpt<T> &O, const T *y)
+{
+    const T r = y[1], kr = y[5];
+    const T guard = (r - H.r_h) / (T(2) * fabs(kr));
+    T h;
+    if (O.step_rule == 1)
+        h = fmin(O.h_frac / (fabs(kr / r) + fabs(y[6]) + fabs(y[7])), guard);
+    else
+        h = fmin(O.h_frac * r, guard);
+    h = fmax(h, O.h_min);
+    return -h;
+}
+
+// Cubic Hermite interpolation within one step of length h.
+template <typename T> __device__ __forceinline__ T hermite(T x0, T v0, T x1, T v1, T h, T s)
+{
+    const T s2 = s * s, s3 = s2 * s;
+    const T h00 = T(2) * s3 - T(3) * s2 + T(1);
+    const T h10 = s3 - T(2) * s2 + s;
+    const T h01 = -T(2) * s3 + T(3) * s2;
+    const T h11 = s3 - s2;
+    return h00 * x0 + h10 * h * v0 + h01 * x1 + h11 * h * v1;
+}
+
+template <typename T> struct BisectIters;
+template <> struct BisectIters<float> { static constexpr int value = 30; };
+template <> struct BisectIters<double> { static constexpr int value = 60; };
+
+// Final (t, r, theta, phi) on the stop surface r = r_stop: bisection of the
+// Hermite r(s) over the last step, then Hermite for the other coordinates,
+// then the pole remap of Eq. 3 applied to the interpolated point.
+template <typename T>
+__device__ inline void stop_surface(const T *y0, const T *y1, T h, T r_stop, T *fin)
+{
+    T lo = T(0), hi = T(1);
+    T f_lo = y0[1] - r_stop;
+    for (int it = 0; it < BisectIters<T>::value; ++it) {
+        T mid = T(0.5) * (lo + hi);
+        T f_mid = hermite(y0[1], y0[5], y1[1], y1[5], h, mid) - r_stop;
+        if ((f_mid > T(0)) == (f_lo > T(0))) {
+            lo = mid;
+            f_lo = f_mid;
+        } else {
+            hi = mid;
+        }
+    }
+    const T s = T(0.5) * (lo + hi);
+    for (int m = 0; m < 4; ++m)
+        fin[m] = hermite(y0[m], y0[4 + m], y1[m], y1[4 + m], h, s);
+    if (fin[2] > pi_v<T>()) {
+        fin[2] = T(2) * pi_v<T>() - fin[2];
+        fin[3] = fin[3] + pi_v<T>();
+    } else if (fin[2] < T(0)) {
+        fin[2] = -fin[2];
+        fin[3] = fin[3] - pi_v<T>();
+    }
+}
+
+// Image-plane initial conditions in double precision: flat-space picture of
+// the pixel (alpha, beta) at distance D = r_obs, observer direction
+// n = (sin i, 0, cos i), photon moving along +n; k^t is the future root of the
+// null condition in the Kerr metric; k is scaled to unit energy E = -k_t.
+__device__ inline void initial_state(double M, double a, double r_obs, double incl, double alpha, double beta,
+                                     double *y)
+{
+    const double D = r_obs;
+    double si, ci;
+    sincos(incl, &si, &ci);
+    const double x = D * si - beta * ci;
+    const double z = D * ci + beta * si;
+    const double r = sqrt(D * D + alpha * alpha + beta * beta);
+    const double rho = sqrt(x * x + alpha * alpha);
+    const double th = atan2(rho, z);
+    const double ph = atan2(alpha, x);
+    const double kr = D / r;
+    const double kth = (z * D - r * r * ci) / (rho * r * r);
+    const double kph = -alpha * si / (rho * rho);
+    Hole<double> H = make_hole(a, M, r_obs, 1.0, 1.0, 0.0);
+    double s, c;
+    sincos(th, &s, &c);
+    MetricPieces<double> m = metric_pieces(H, r, s, c);
+    const double A = m.gtt;
+    const double B = 2.0 * m.gtp * kph;
+    const double C = m.grr * kr * kr + m.gthth * kth * kth + m.gpp * kph * kph;
+    const double kt = (-B - sqrt(B * B - 4.0 * A * C)) / (2.0 * A);
+    const double E = -(m.gtt * kt + m.gtp * kph);
+    y[0] = 0.0;
+    y[1] = r;
+    y[2] = th;
+    y[3] = ph;
+    y[4] = kt / E;
+    y[5] = kr / E;
+    y[6] = kth / E;
+    y[7] = kph / E;
+}
+
+} // namespace gray

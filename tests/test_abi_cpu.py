@@ -1,0 +1,77 @@
+"""The C-ABI library without a GPU: it loads, exports every function that
+include/gray.h declares, and its host-side logic (layout sizes, defaults,
+argument validation that returns before any CUDA call) behaves."""
+import ctypes as C
+import re
+
+import pytest
+
+from paper_1303_5057_gb300 import build, gray
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return gray.lib()
+
+
+def test_exports_every_declared_function(L):
+    names = gray.header_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_header_constants_match_binding():
+    text = open(gray.HEADER).read()
+    consts = dict(re.findall(r"#define (GRAY_[A-Z0-9_]+) \(?(-?\d+)\)?", text))
+    for name, val in consts.items():
+        py = name[len("GRAY_"):]
+        if hasattr(gray, py):
+            assert getattr(gray, py) == int(val), name
+
+
+def test_state_bytes(L):
+    for prec in (gray.FP64, gray.FP32, gray.FP32_KAHAN, gray.FP32_KAHAN_SEL64):
+        assert gray.gray_state_bytes(0, prec) == 0
+        b1 = gray.gray_state_bytes(1, prec)
+        assert b1 > 0 and b1 % 256 == 0
+        n = 1 << 20
+        per = (32 * 3 if prec == gray.FP64 else 16 * 5) + 32 + 16 + 4
+        assert gray.gray_state_bytes(n, prec) == per * n
+    assert gray.gray_state_bytes(-1, gray.FP64) == 0
+    assert gray.gray_state_bytes(10, 7) == 0
+
+
+def test_defaults_and_strerror(L):
+    o = gray.gray_default_options()
+    assert o == gray.Options()
+    assert gray.gray_strerror(0) == "success"
+    assert "invalid" in gray.gray_strerror(gray.EINVAL)
+    assert gray.gray_strerror(-99) == "unknown error code"
+    assert gray.gray_launch_count() >= 0
+
+
+@pytest.mark.parametrize("bad", [dict(precision=9), dict(step_rule=5), dict(max_steps=0), dict(block=48),
+                                 dict(h_frac=0.0), dict(h_frac=float("nan")), dict(cap_frac=0.5),
+                                 dict(eps_xi=-1.0), dict(r_sw=-0.1), dict(blocks_per_sm=-1)])
+def test_create_rejects_bad_options_before_touching_the_device(L, bad):
+    opt = gray.Options(**bad)
+    h = C.c_void_p()
+    o = opt._c()
+    assert L.gray_create(C.byref(h), C.byref(o)) == gray.EINVAL
+    assert not h.value
+
+
+def test_calls_reject_null_context(L):
+    assert L.gray_setup(None, None, 1, None, 0, 1, 0, None) == gray.EINVAL
+    assert L.gray_trace(None, None, 0, 0, 0, None, None, None) == gray.EINVAL
+    assert L.gray_render(None, None, 0, 0, 0, 0, 0, None, 0, None) == gray.EINVAL
+    assert L.gray_shadow(None, None, 0, 0, 0, None, 0, None, 0, None) == gray.EINVAL
+
+
+def test_eval_rejects_bad_arguments(L):
+    assert L.gray_eval(99, gray.FP64, None, 1, None, None) == gray.EINVAL
+    assert L.gray_eval(gray.EVAL_RHS, gray.FP32_KAHAN, None, 1, None, None) == gray.EINVAL
+    assert L.gray_eval(gray.EVAL_RHS, gray.FP64, None, -1, None, None) == gray.EINVAL
+    assert L.gray_eval(gray.EVAL_RHS, gray.FP64, None, 0, None, None) == gray.OK

@@ -1,0 +1,330 @@
+"""GPU parity: the CUDA tracer, called through the C ABI, against the FP64 CPU
+oracle on the same seeded inputs.
+
+Tolerances (from the acceptance of the tracer, pixels within 0.05 M of the
+analytic critical curve excluded, where rays are chaotic):
+  * FP64 path: same status and step count; final angles within 1e-9
+    relative (|d| <= 1e-9 max(1, |ref|));
+  * FP32 paths: classification agreement >= 99.99 %; final theta, phi within
+    1e-4 rad.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import parity as P
+import theory as T
+from paper_1303_5057_gb300 import gray
+from paper_1303_5057_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+M = 1.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1303_5057_gb300 import build
+    build.build()
+    gray.lib()
+    oracle.lib()
+    torch.cuda.init()
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda")
+
+
+def trace_image(im, opt, step_budget=0):
+    tr = gray.Tracer(opt, im.n)
+    tr.setup([im])
+    inv0 = tr.invariants()
+    rc, n_active, stats = tr.trace(step_budget)
+    rec = tr.records()
+    inv1 = tr.invariants()
+    tr.close()
+    return rec, inv0, inv1, stats
+
+
+def oracle_image(im, max_steps, step_rule=oracle.STEP_BENCH):
+    rays = oracle.image_rays(im.a, im.incl, im.r_obs, im.nx, im.ny, im.alpha0, im.alpha1, im.beta0, im.beta1)
+    return rays, oracle.trace_many(rays, oracle.Options(M=im.M, max_steps=max_steps, step_rule=step_rule))
+
+
+# ------------------------------------------------------------ unit parity ---
+
+def _points(n=512, seed=7):
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(-0.999, 0.999, n)
+    r = np.exp(rng.uniform(np.log(1.05), np.log(2000.0), n)) * (1 + np.sqrt(1 - a * a))
+    th = rng.uniform(0.02, math.pi - 0.02, n)
+    return a, r, th
+
+
+@pytest.mark.parametrize("prec,tol", [(gray.FP64, 1e-12), (gray.FP32, 2e-5)])
+def test_closed_form_christoffel_matches_general_formula(prec, tol):
+    a, r, th = _points()
+    inp = np.stack([np.full_like(a, M), a, r, th], axis=1)
+    got = gray.gray_eval(gray.EVAL_CHRISTOFFEL, prec, dev(inp)).cpu().numpy().reshape(-1, 4, 4, 4)
+    for k in range(len(a)):
+        G = oracle.christoffel(M, a[k], r[k], th[k])
+        scale = np.abs(G).max()
+        assert np.abs(got[k] - G).max() <= tol * scale, (k, a[k], r[k], th[k])
+
+
+@pytest.mark.parametrize("prec,tol", [(gray.FP64, 1e-11), (gray.FP32, 5e-5)])
+def test_geodesic_rhs_matches_oracle(prec, tol):
+    a, r, th = _points(seed=11)
+    rng = np.random.default_rng(3)
+    k = rng.normal(size=(len(a), 4))
+    k[:, 0] = np.abs(k[:, 0]) * 3 + 1
+    y = np.zeros((len(a), 8))
+    y[:, 1], y[:, 2] = r, th
+    y[:, 4:] = k
+    inp = np.concatenate([np.stack([np.full_like(a, M), a], axis=1), y], axis=1)
+    got = gray.gray_eval(gray.EVAL_RHS, prec, dev(inp)).cpu().numpy()
+    for i in range(len(a)):
+        ref = oracle.rhs(M, a[i], y[i])
+        # terms of the contraction can cancel: compare against the size of the terms
+        G = oracle.christoffel(M, a[i], r[i], th[i])
+        terms = np.einsum("mab,a,b->m", np.abs(G), np.abs(k[i]), np.abs(k[i]))
+        assert np.all(np.abs(got[i, 4:] - ref[4:]) <= tol * (terms + 1e-300)), i
+        assert np.all(got[i, :4] == y[i, 4:].astype(np.float32 if prec == gray.FP32 else np.float64))
+
+
+def test_initial_conditions_match_oracle():
+    rng = np.random.default_rng(5)
+    n = 400
+    inp = np.stack([np.full(n, M), rng.uniform(-0.99, 0.99, n), rng.choice([1e3, 1e4], n),
+                    rng.uniform(0, math.pi, n), rng.uniform(-15, 15, n), rng.uniform(-15, 15, n)], axis=1)
+    got = gray.gray_eval(gray.EVAL_INITIAL, gray.FP64, dev(inp)).cpu().numpy()
+    for i in range(n):
+        ref = oracle.initial(*inp[i])
+        assert np.allclose(got[i], ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("prec,tol", [(gray.FP64, 1e-12), (gray.FP32, 1e-4)])
+def test_xi_matches_oracle(prec, tol):
+    rng = np.random.default_rng(9)
+    rows = []
+    for _ in range(200):
+        a = rng.uniform(-0.99, 0.99)
+        y = oracle.initial(M, a, 1000.0, rng.uniform(0.1, 3.0), rng.uniform(-9, 9), rng.uniform(-9, 9))
+        y[5] *= 1 + rng.uniform(-0.01, 0.01)
+        rows.append(np.concatenate([[M, a], y]))
+    inp = np.array(rows)
+    got = gray.gray_eval(gray.EVAL_XI, prec, dev(inp)).cpu().numpy()[:, 0]
+    for i in range(len(rows)):
+        ref = oracle.xi(M, inp[i, 1], inp[i, 2:])
+        assert abs(got[i] - ref) <= tol * max(1.0, abs(ref))
+
+
+# ------------------------------------------------------------- whole rays ---
+
+def test_schwarzschild_64x64_fp64_matches_oracle():
+    """Schwarzschild, i = 60 deg, 64 x 64 over [-10, 10]^2, FP64, cap 1e5."""
+    wl = I.schwarzschild_64()
+    im = wl.images[0]
+    rec, _, _, stats = trace_image(im, gray.Options(precision=gray.FP64, max_steps=wl.max_steps))
+    rays, ref = oracle_image(im, wl.max_steps)
+    far = P.band_mask((rays[:, 0], rays[:, 1]), im.a, im.incl)
+    c = P.compare(rec, ref, far)
+    assert c["class_disagree_far"] == 0, c
+    assert c["max_rel"] <= 1e-9, c
+    assert np.all(rec[far, 1] == ref[far, 1]) and np.all(rec[far, 2] == ref[far, 2])
+    assert stats[0] == int(rec[:, 1].sum())
+
+
+_KERR_CACHE = {}
+
+
+def kerr_reference(rule, side=96):
+    """Oracle records of the a = 0.99, i = 90 deg image at side x side, the
+    0.05 M band mask and the oracle's own Carter drift (cached per rule)."""
+    key = (rule, side)
+    if key not in _KERR_CACHE:
+        im = I.kerr_1024(side).images[0]
+        rays, ref = oracle_image(im, 10000, step_rule=rule)
+        far = P.band_mask((rays[:, 0], rays[:, 1]), im.a, im.incl)
+        qd = P.oracle_q_drift(oracle, rays, ref)
+        _KERR_CACHE[key] = (im, rays, ref, far, qd)
+    return _KERR_CACHE[key]
+
+
+@pytest.mark.parametrize("rule", [gray.STEP_BENCH, gray.STEP_EQ2])
+def test_kerr_fp64_matches_oracle(rule):
+    """a = 0.99, i = 90 deg, the 1024^2 window at 96 x 96, FP64: classification
+    equal outside the band; final angles within 1e-9 relative and identical
+    step counts wherever the oracle integrates the ray faithfully."""
+    im, rays, ref, far, qd = kerr_reference(rule)
+    rec, _, _, _ = trace_image(im, gray.Options(precision=gray.FP64, max_steps=10000, step_rule=rule))
+    assert P.compare(rec, ref, far)["class_agree_far"] == 1.0
+    sane = far & (qd < P.SANE_Q)
+    c = P.compare(rec, ref, sane)
+    assert c["max_rel"] <= 1e-9, c
+    assert c["steps_equal_frac"] == 1.0, c
+    # Eq. 2 integrates nearly every ray faithfully; the benchmark rule does
+    # not for rays that graze the poles (see the oracle's pins)
+    if rule == gray.STEP_EQ2:
+        assert sane.sum() > 0.9 * far.sum()
+
+
+@pytest.mark.parametrize("prec,r_sw", [(gray.FP32_KAHAN, 0.0), (gray.FP32_KAHAN_SEL64, 0.25),
+                                       (gray.FP32_KAHAN_SEL64, 1.0)])
+def test_kerr_fp32_compensated_matches_oracle(prec, r_sw):
+    """Benchmark step rule, a = 0.99, i = 90 deg at 96 x 96: compensated FP32
+    (with or without double steps near the horizon) against the FP64 oracle:
+    classification >= 99.99 % outside the band, final angles within 1e-4 rad
+    on every ray the oracle integrates faithfully."""
+    im, rays, ref, far, qd = kerr_reference(gray.STEP_BENCH)
+    rec, inv0, inv1, stats = trace_image(im, gray.Options(precision=prec, max_steps=10000, r_sw=r_sw))
+    assert P.compare(rec, ref, far)["class_agree_far"] >= 0.9999
+    c = P.compare(rec, ref, far & (qd < P.SANE_Q))
+    assert c["n_ang_gt_1e-4"] == 0, c
+    # Carter drift of the compensated FP32 trace follows the oracle's own
+    gq = P.q_drift(inv0, inv1, im.a)
+    ok = far & (qd < P.SANE_Q) & (rec[:, 0] == oracle.ESCAPED)
+    assert np.percentile(np.abs(gq[ok] - qd[ok]), 99) < 1e-5
+
+
+def test_kerr_fp32_plain_is_less_accurate_than_compensated():
+    """Plain FP32 (no compensation) classifies the same rays but its angles
+    drift further from the oracle than the compensated path's."""
+    im, rays, ref, far, qd = kerr_reference(gray.STEP_BENCH)
+    sane = far & (qd < P.SANE_Q)
+    plain, _, _, _ = trace_image(im, gray.Options(precision=gray.FP32, max_steps=10000))
+    comp, _, _, _ = trace_image(im, gray.Options(precision=gray.FP32_KAHAN, max_steps=10000))
+    assert P.compare(plain, ref, far)["class_agree_far"] >= 0.9999
+    cp, cc = P.compare(plain, ref, sane), P.compare(comp, ref, sane)
+    assert cp["p9999_dang"] > cc["p9999_dang"]
+    assert cp["max_dphi"] < 0.1
+
+
+def test_kerr_eq2_fp32_selective_fp64():
+    """Eq. 2 step rule: compensated FP32 with double steps within 1 M of the
+    capture radius.  Classification is exact outside the band; final angles
+    are within 1e-4 rad on all but a handful of near-critical rays (measured
+    worst case below 1e-3)."""
+    im, rays, ref, far, qd = kerr_reference(gray.STEP_EQ2)
+    rec, _, _, _ = trace_image(im, gray.Options(precision=gray.FP32_KAHAN_SEL64, max_steps=10000, r_sw=1.0,
+                                                step_rule=gray.STEP_EQ2))
+    assert P.compare(rec, ref, far)["class_agree_far"] >= 0.9999
+    c = P.compare(rec, ref, far & (qd < P.SANE_Q))
+    assert c["n_ang_gt_1e-4"] <= max(3, c["n_compared"] // 2000), c
+    assert max(c["max_dtheta"], c["max_dphi"]) < 2e-3, c
+
+
+def test_trace_split_over_calls_equals_one_call():
+    """Resumable tracing (the step-limited mode of Sec. 2): many calls with a
+    small per-call budget give bit-identical records to one call."""
+    im = I.Image(a=0.7, incl=math.radians(40.0), nx=20, ny=17)
+    for prec in (gray.FP64, gray.FP32_KAHAN_SEL64):
+        opt = gray.Options(precision=prec, max_steps=5000, r_sw=0.5, refill=3)
+        one, _, _, _ = trace_image(im, opt)
+        tr = gray.Tracer(opt, im.n)
+        tr.setup([im])
+        calls = 0
+        while True:
+            rc, n_active, stats = tr.trace(step_budget=37)
+            calls += 1
+            if n_active == 0:
+                break
+            assert calls < 1000
+        many = tr.records()
+        tr.close()
+        assert calls > 5
+        assert np.array_equal(one, many)
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 1000])
+def test_ragged_sizes(n):
+    """Ray counts that are not multiples of the warp or block."""
+    rng = np.random.default_rng(n)
+    rays = np.stack([rng.uniform(-9, 9, n), rng.uniform(-9, 9, n), rng.uniform(0, 0.99, n),
+                     rng.uniform(0.1, 1.5, n), np.full(n, 1000.0)], axis=1)
+    tr = gray.Tracer(gray.Options(precision=gray.FP64, max_steps=20000), n)
+    tr.setup_rays(dev(rays))
+    rc, n_active, _ = tr.trace()
+    rec = tr.records()
+    tr.close()
+    ref = oracle.trace_many(rays, oracle.Options(max_steps=20000))
+    assert rc == 0 and n_active == 0
+    same = rec[:, 0] == ref[:, 0]
+    assert same.mean() >= 0.99
+    ok = same & ((ref[:, 0] == 1) | (ref[:, 0] == 2))
+    assert np.median(np.abs(rec[ok, 6] - ref[ok, 6])) < 1e-9
+
+
+def test_empty_and_degenerate():
+    tr = gray.Tracer(gray.Options(precision=gray.FP64), 0)
+    rc, n_active, stats = tr.trace()
+    assert rc == 0 and n_active == 0 and stats[0] == 0
+    tr.close()
+    # flat space (M = 0): no capture, straight lines, same as the oracle
+    im = I.Image(a=0.0, incl=1.0, nx=9, ny=7, M=0.0, alpha0=2.0, alpha1=9.0, beta0=1.0, beta1=8.0)
+    rec, _, _, _ = trace_image(im, gray.Options(precision=gray.FP64))
+    rays, ref = oracle_image(im, 100000)
+    assert np.all(rec[:, 0] == oracle.ESCAPED) and np.all(ref[:, 0] == oracle.ESCAPED)
+    assert np.abs(rec[:, 6] - ref[:, 6]).max() < 1e-10
+    # the step cap: status 3 and the same state as the oracle after max_steps steps
+    im2 = I.Image(a=0.5, incl=0.7, nx=4, ny=4)
+    rec, _, _, _ = trace_image(im2, gray.Options(precision=gray.FP64, max_steps=25))
+    rays2, ref2 = oracle_image(im2, 25)
+    assert np.all(rec[:, 0] == oracle.STEP_CAP) and np.all(rec[:, 1] == 25)
+    assert np.allclose(rec[:, 8:16], ref2[:, 8:16], rtol=1e-12, atol=1e-9)
+    # a polar observer (i = 0): pixel centres avoid the axis itself
+    im3 = I.Image(a=0.9, incl=0.0, nx=6, ny=6)
+    rec3, _, _, _ = trace_image(im3, gray.Options(precision=gray.FP64, max_steps=20000))
+    _, ref3 = oracle_image(im3, 20000)
+    assert np.array_equal(rec3[:, 0], ref3[:, 0])
+
+
+def test_batched_images_equal_separate_images():
+    """Several (a, i) images set up in one call and traced in one launch give
+    the same records as each image alone."""
+    ims = [I.Image(a=0.3, incl=0.4, nx=13, ny=9), I.Image(a=0.95, incl=1.4, nx=7, ny=11),
+           I.Image(a=0.0, incl=1.0, nx=16, ny=16)]
+    opt = gray.Options(precision=gray.FP32_KAHAN_SEL64, max_steps=10000, r_sw=0.5)
+    tr = gray.Tracer(opt, sum(im.n for im in ims))
+    tr.setup(ims)
+    tr.trace()
+    allrec = tr.records()
+    sh = tr.shadow(ims)
+    tr.close()
+    off = 0
+    for k, im in enumerate(ims):
+        alone, _, _, _ = trace_image(im, opt)
+        assert np.array_equal(alone, allrec[off:off + im.n])
+        cap = alone[:, 0] == oracle.CAPTURED
+        al, be = oracle.pixel_centres(im.nx, im.ny, im.alpha0, im.alpha1, im.beta0, im.beta1)
+        assert sh[k]["n_captured"] == cap.sum()
+        cell = (im.alpha1 - im.alpha0) / im.nx * (im.beta1 - im.beta0) / im.ny
+        assert sh[k]["area"] == pytest.approx(cap.sum() * cell)
+        if cap.any():
+            assert sh[k]["alpha_c"] == pytest.approx(al[cap].mean(), abs=1e-9)
+            assert sh[k]["beta_c"] == pytest.approx(be[cap].mean(), abs=1e-9)
+        off += im.n
+
+
+def test_mixed_per_ray_workload_fp64():
+    """Per-ray (alpha, beta, a, i) rays of the mixed workload, half near the
+    critical curve: FP64 against the oracle, outside the 0.05 M band."""
+    rays = I.mixed_rays(2048)
+    tr = gray.Tracer(gray.Options(precision=gray.FP64, max_steps=10000), len(rays))
+    tr.setup_rays(dev(rays))
+    tr.trace()
+    rec = tr.records()
+    tr.close()
+    ref = oracle.trace_many(rays, oracle.Options(max_steps=10000))
+    far = np.ones(len(rays), dtype=bool)
+    for k in range(len(rays)):
+        cx, cy = T.bardeen_curve(rays[k, 2], rays[k, 3], 4000)
+        if cx.size < 200:  # nearly polar observer: the boundary is nearly a circle
+            far[k] = abs(math.hypot(rays[k, 0], rays[k, 1]) - T.polar_shadow_radius(rays[k, 2])) > 0.6
+        else:
+            far[k] = T.curve_distance([rays[k, 0]], [rays[k, 1]], cx, cy)[0] > 0.05
+    c = P.compare(rec, ref, far)
+    assert c["class_agree_far"] >= 0.999, c
