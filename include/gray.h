@@ -207,6 +207,35 @@ int gray_shadow(gray_ctx *ctx, const void *state_dev, size_t state_bytes, int64_
                 int64_t first_ray, const gray_image *images_host, int32_t n_images,
                 gray_shadow_info *out_dev, size_t out_bytes, void *stream);
 
+/* Maximum number of images one gray_setup_noalloc call accepts. */
+#define GRAY_NOALLOC_MAX_IMAGES 4096
+
+/* gray_setup for callers that must not allocate device memory -- for
+ * example a simulation code that owns the whole device memory budget through
+ * its own pool, or a caller whose allocator calls are forbidden in its
+ * time-critical loop.  gray_setup uploads the image table through a
+ * temporary stream-ordered allocation on every call and needs a context,
+ * whose creation allocates; this entry point needs neither.  The paper has no
+ * counterpart: it is an interface convenience of this library.
+ *
+ * It writes the same initial states as gray_setup (bit for bit) for a
+ * buffer laid out for `precision`.  The image table is copied into a
+ * file-scope device array of GRAY_NOALLOC_MAX_IMAGES entries (80 bytes each,
+ * 320 KB) that every device loading the library holds until the process
+ * exits; n_images above that maximum is rejected with GRAY_EINVAL before any
+ * work is enqueued.  On the first call on a device the library looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current and
+ * caches it; make that first call before any stream capture.  The array is
+ * shared by all calls and keeps the last call's table: calls that overlap on
+ * the GPU (on different streams, or from several threads) race on it, so
+ * order them on one stream or synchronise between them.  No cudaMalloc,
+ * cudaFree or other allocating routine is called.
+ * Errors: GRAY_EINVAL (bad precision, image or range; too many images),
+ * GRAY_ECUDA. */
+int gray_setup_noalloc(int32_t precision, const gray_image *images_host, int32_t n_images,
+                       void *state_dev, size_t state_bytes, int64_t n_state, int64_t first_ray,
+                       void *stream);
+
 /* Evaluate one device function of the tracer on n inputs, in the arithmetic
  * of `precision` (GRAY_FP64 or GRAY_FP32), for unit parity tests: in_dev and
  * out_dev are n rows of doubles laid out as listed at GRAY_EVAL_*.

@@ -1115,6 +1115,78 @@ int gray_eval(int32_t what, int32_t precision, const double *in, int64_t n, doub
     return check_launch();
 }
 
+// ---- setup without allocation ---------------------------------------------
+// The image table of gray_setup_noalloc lives in this file-scope device
+// array; host code reaches it only through the address that
+// cudaGetSymbolAddress returns for the current device (cached per device).
+static __device__ __align__(256) ImageDev g_noalloc_images[GRAY_NOALLOC_MAX_IMAGES];
+
+namespace {
+constexpr int kMaxDevices = 256;
+std::atomic<void *> g_noalloc_addr[kMaxDevices];
+} // namespace
+
+int gray_setup_noalloc(int32_t precision, const gray_image *images, int32_t n_images, void *state,
+                       size_t state_bytes, int64_t n_state, int64_t first_ray, void *stream)
+{
+    if (precision < GRAY_FP64 || precision > GRAY_FP32_KAHAN_SEL64)
+        return GRAY_EINVAL;
+    if (!images || n_images < 1 || n_images > GRAY_NOALLOC_MAX_IMAGES || !state || n_state < 0 || first_ray < 0)
+        return GRAY_EINVAL;
+    if (state_bytes < gray_state_bytes(n_state, precision))
+        return GRAY_EINVAL;
+    int rc;
+    int64_t total = 0;
+    for (int k = 0; k < n_images; ++k) {
+        if ((rc = validate_image(images[k])))
+            return rc;
+        total += (int64_t)images[k].nx * images[k].ny;
+    }
+    if (first_ray + total > n_state)
+        return GRAY_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return GRAY_ECUDA;
+    void *table = g_noalloc_addr[dev].load(std::memory_order_acquire);
+    if (!table) {
+        if (cudaGetSymbolAddress(&table, g_noalloc_images) != cudaSuccess || !table)
+            return GRAY_ECUDA;
+        g_noalloc_addr[dev].store(table, std::memory_order_release);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // Fill the table in chunks through a small stack buffer: a copy from
+    // pageable memory has consumed its source when cudaMemcpyAsync returns.
+    constexpr int kChunk = 64;
+    ImageDev chunk[kChunk];
+    int64_t first = 0;
+    for (int k0 = 0; k0 < n_images; k0 += kChunk) {
+        const int m = (n_images - k0) < kChunk ? (n_images - k0) : kChunk;
+        for (int j = 0; j < m; ++j) {
+            const gray_image &im = images[k0 + j];
+            ImageDev &d = chunk[j];
+            d.a = im.a;
+            d.M = im.M;
+            d.r_obs = im.r_obs;
+            d.incl = im.incl;
+            d.a0 = im.alpha0;
+            d.da = (im.alpha1 - im.alpha0) / im.nx;
+            d.b0 = im.beta0;
+            d.db = (im.beta1 - im.beta0) / im.ny;
+            d.nx = im.nx;
+            d.ny = im.ny;
+            d.first = first;
+            first += (int64_t)im.nx * im.ny;
+        }
+        if (cudaMemcpyAsync((ImageDev *)table + k0, chunk, sizeof(ImageDev) * (size_t)m, cudaMemcpyHostToDevice,
+                            s) != cudaSuccess)
+            return GRAY_ECUDA;
+    }
+    StateView v = make_view(state, n_state, precision);
+    setup_images_kernel<<<grid_for(total, 256), 256, 0, s>>>((const ImageDev *)table, n_images, total, first_ray, v,
+                                                           precision);
+    return check_launch();
+}
+
 const char *gray_strerror(int code)
 {
     switch (code) {

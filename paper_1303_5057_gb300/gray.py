@@ -27,6 +27,7 @@ STEP_BENCH, STEP_EQ2 = 0, 1
 RENDER_PIXELS64, RENDER_PIXELS32, RENDER_RECORD, RENDER_INVARIANTS = 0, 1, 3, 4
 EVAL_CHRISTOFFEL, EVAL_RHS, EVAL_INITIAL, EVAL_XI = 0, 1, 2, 3
 RECORD = 17
+NOALLOC_MAX_IMAGES = 4096
 
 PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp32_kahan": FP32_KAHAN, "fp32_kahan_sel64": FP32_KAHAN_SEL64}
 
@@ -99,6 +100,8 @@ def lib():
     L.gray_destroy.restype = None
     L.gray_setup.argtypes = [vp, C.POINTER(_Image), i32, vp, sz, i64, i64, vp]
     L.gray_setup.restype = C.c_int
+    L.gray_setup_noalloc.argtypes = [i32, C.POINTER(_Image), i32, vp, sz, i64, i64, vp]
+    L.gray_setup_noalloc.restype = C.c_int
     L.gray_setup_rays.argtypes = [vp, vp, i64, C.c_double, vp, sz, i64, i64, vp]
     L.gray_setup_rays.restype = C.c_int
     L.gray_trace.argtypes = [vp, vp, sz, i64, i64, C.POINTER(i64), C.POINTER(i64), vp]
@@ -187,6 +190,16 @@ def gray_setup(ctx, images, state, n_state, first_ray=0, stream=None):
     arr = _images(images)
     return _check(lib().gray_setup(ctx, arr, len(images), _ptr(state), state.numel() * state.element_size(),
                                    int(n_state), int(first_ray), _stream(stream)), "gray_setup")
+
+
+def gray_setup_noalloc(precision, images, state, n_state, first_ray=0, stream=None):
+    """gray_setup without a context and without any device allocation: the
+    image table goes through a fixed device array of GRAY_NOALLOC_MAX_IMAGES
+    entries inside the library (for callers that cannot allocate)."""
+    arr = _images(images)
+    return _check(lib().gray_setup_noalloc(int(precision), arr, len(images), _ptr(state),
+                                           state.numel() * state.element_size(), int(n_state), int(first_ray),
+                                           _stream(stream)), "gray_setup_noalloc")
 
 
 def gray_setup_rays(ctx, rays, M, state, n_state, first_ray=0, stream=None):
