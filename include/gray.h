@@ -177,7 +177,12 @@ int gray_setup_rays(gray_ctx *ctx, const double *rays_dev, int64_t n, double M,
  * for this call: steps taken, Euler redos, steps promoted to double, rays
  * still active.  Returns 0 when no ray is active, 1 when some remain or when
  * no host output was requested (the count is then unknown), or an error
- * (GRAY_EINVAL, GRAY_ECUDA). */
+ * (GRAY_EINVAL, GRAY_ECUDA).
+ * In GRAY_FP32_KAHAN_SEL64 the call alternates a single-precision pass over
+ * the buffer with a double-precision pass over the rays that entered the
+ * zone near the horizon, and waits for the stream between passes to read two
+ * counters; the other precisions are one launch and do not wait unless a
+ * host output was requested. */
 int gray_trace(gray_ctx *ctx, void *state_dev, size_t state_bytes, int64_t n_state,
                int64_t step_budget, int64_t *n_active_host, int64_t *stats_host, void *stream);
 

@@ -50,9 +50,10 @@ __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_
 //   F  final position on the stop surface  float4 / d4
 //   P  per-ray constants (a, M, r_obs, 0)  d4
 //   S0 (status, steps, Euler redos, pole remaps)  int4
-//   S1 steps promoted to double         int
+//   S1 (steps in double, call epoch, steps in that call, flags)  int4
+//   L  hand-off list of ray indices (selective-double mode)  int
 struct Layout {
-    size_t X, K, CX, CK, F, P, S0, S1, total;
+    size_t X, K, CX, CK, F, P, S0, S1, L, total;
 };
 
 inline bool is_f64(int prec) { return prec == GRAY_FP64; }
@@ -82,6 +83,8 @@ Layout make_layout(int64_t n, int prec)
     L.S0 = off;
     off = align256(off + 16 * un);
     L.S1 = off;
+    off = align256(off + 16 * un);
+    L.L = off;
     off = align256(off + 4 * un);
     L.total = off;
     return L;
@@ -91,7 +94,8 @@ struct StateView {
     char *X, *K, *CX, *CK, *F;
     d4 *P;
     int4 *S0;
-    int *S1;
+    int4 *S1;
+    int *L;
 };
 
 StateView make_view(void *base, int64_t n, int prec)
@@ -106,7 +110,8 @@ StateView make_view(void *base, int64_t n, int prec)
     v.F = b + L.F;
     v.P = (d4 *)(b + L.P);
     v.S0 = (int4 *)(b + L.S0);
-    v.S1 = (int *)(b + L.S1);
+    v.S1 = (int4 *)(b + L.S1);
+    v.L = (int *)(b + L.L);
     return v;
 }
 
@@ -130,12 +135,14 @@ __device__ __forceinline__ void st_f4(void *p, int64_t i, float x, float y, floa
 
 // Workspace of one context (device memory, zeroed before each trace).
 struct Workspace {
-    unsigned long long head;   // next ray index handed out by the queue
-    unsigned long long steps;  // steps taken in this call
-    unsigned long long euler;  // Euler redos in this call
-    unsigned long long fp64;   // steps promoted to double in this call
-    unsigned long long active; // rays left active by this call
-    unsigned long long pad[3];
+    unsigned long long head;    // next ray (or list slot) handed out by the queue of a pass
+    unsigned long long steps;   // steps taken in this call
+    unsigned long long euler;   // Euler redos in this call
+    unsigned long long fp64;    // steps taken in double by the selective mode in this call
+    unsigned long long active;  // rays left active by this call
+    unsigned long long handoff; // rays appended to the hand-off list in this round
+    unsigned long long demoted; // rays returned to single precision in this round
+    unsigned long long pad;
 };
 
 } // namespace
@@ -146,6 +153,7 @@ struct gray_ctx {
     Workspace *ws_host = nullptr; // pinned host mirror
     int device = 0;
     int num_sms = 0;
+    int epoch = 0; // gray_trace calls made with this context
 };
 
 namespace {
@@ -184,7 +192,7 @@ __device__ void store_initial(const StateView &v, int prec, int64_t i, const dou
     }
     st_d4(v.P, i, a, M, r_obs, 0.0);
     v.S0[i] = make_int4(GRAY_RAY_ACTIVE, 0, 0, 0);
-    v.S1[i] = 0;
+    v.S1[i] = make_int4(0, 0, 0, 0);
 }
 
 __global__ void setup_images_kernel(const ImageDev *imgs, int n_images, int64_t total, int64_t first_ray,
@@ -352,8 +360,22 @@ __device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, 
 }
 
 // --------------------------------------------------------------------------
-// Persistent trace kernel
+// Persistent trace kernels
 // --------------------------------------------------------------------------
+//
+// Single-precision modes run trace32_kernel over every ray of the buffer.
+// In GRAY_FP32_KAHAN_SEL64 a ray that reaches the double zone (r below
+// cap_frac r_h + r_sw at the start of a step) is handed off: its state is
+// stored and its index appended to the hand-off list.  trace64_kernel then
+// runs the listed rays in double precision, 32 to a warp, until they stop
+// or climb out of the zone (r above cap_frac r_h + 2 r_sw), when they return
+// to single precision for the next pass.  The FP64 pipe of this part runs at
+// 1/64 of the FP32 rate, so a double step must never hold a warp of
+// single-precision lanes; the hand-off keeps the two populations apart and
+// the single-precision kernel free of double-precision registers.
+// GRAY_FP64 runs trace64_kernel over every ray, with double planes.
+
+enum : int { FLAG_DOUBLE_MODE = 1, FLAG_DOUBLE_REPR = 2 };
 
 struct TraceArgs {
     StateView v;
@@ -361,74 +383,76 @@ struct TraceArgs {
     int64_t budget; // per-call step budget per ray, <= 0: none
     int max_steps;
     int refill;
-    double h_frac, h_min, eps_xi, cap_frac, r_esc_frac, r_sw;
     int step_rule;
+    int epoch; // call counter: S1.y == epoch means S1.z counts this call's steps
+    double h_frac, h_min, eps_xi, cap_frac, r_esc_frac, r_sw;
     Workspace *ws;
 };
 
 template <int MODE> struct ModeTraits {
-    using T = float;
     static constexpr bool kahan = (MODE == GRAY_FP32_KAHAN || MODE == GRAY_FP32_KAHAN_SEL64);
     static constexpr bool sel64 = (MODE == GRAY_FP32_KAHAN_SEL64);
 };
-template <> struct ModeTraits<GRAY_FP64> {
-    using T = double;
-    static constexpr bool kahan = false;
-    static constexpr bool sel64 = false;
-};
 
-// The double step used for promoted steps of the selective mode, kept out of
-// line so its registers do not enlarge the single-precision hot loop.
-__device__ __noinline__ int step_promoted(const Hole<double> *H, const StepOpt<double> *O, float *y, float *c,
-                                          float *fin, int *euler, int *remaps)
+// Warp-aggregated counter increment (warp-uniform call).
+__device__ __forceinline__ unsigned long long warp_count(unsigned long long *ctr, bool pred, int lane,
+                                                         int *rank_out)
 {
-    double yd[8], cd[8], find[4];
-    for (int m = 0; m < 8; ++m) {
-        yd[m] = (double)y[m] - (double)c[m];
-        cd[m] = 0.0;
+    const unsigned FULL = 0xffffffffu;
+    const unsigned m = __ballot_sync(FULL, pred);
+    unsigned long long base = 0;
+    if (m) {
+        const int leader = __ffs(m) - 1;
+        if (lane == leader)
+            base = atomicAdd(ctr, (unsigned long long)__popc(m));
+        base = __shfl_sync(FULL, base, leader);
     }
-    int e = *euler, rm = *remaps;
-    int st = step_once<double, false>(*H, *O, yd, cd, find, e, rm);
-    *euler = e;
-    *remaps = rm;
-    for (int m = 0; m < 8; ++m) {
-        y[m] = (float)yd[m];
-        c[m] = (float)((double)y[m] - yd[m]);
-    }
-    for (int m = 0; m < 4; ++m)
-        fin[m] = (float)find[m];
-    return st;
+    *rank_out = __popc(m & ((1u << lane) - 1u));
+    return base;
 }
 
-template <int MODE> __global__ void trace_kernel(TraceArgs A)
+template <typename T>
+__device__ __forceinline__ void warp_stats(const TraceArgs &A, int lane, unsigned long long steps,
+                                           unsigned long long euler, unsigned long long fp64)
 {
-    using T = typename ModeTraits<MODE>::T;
+    const unsigned FULL = 0xffffffffu;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        steps += __shfl_xor_sync(FULL, steps, off);
+        euler += __shfl_xor_sync(FULL, euler, off);
+        fp64 += __shfl_xor_sync(FULL, fp64, off);
+    }
+    if (lane == 0) {
+        if (steps)
+            atomicAdd(&A.ws->steps, steps);
+        if (euler)
+            atomicAdd(&A.ws->euler, euler);
+        if (fp64)
+            atomicAdd(&A.ws->fp64, fp64);
+    }
+}
+
+// Single-precision persistent tracer (modes FP32, FP32_KAHAN, FP32_KAHAN_SEL64).
+template <int MODE> __global__ void __launch_bounds__(128) trace32_kernel(TraceArgs A)
+{
     constexpr bool KAHAN = ModeTraits<MODE>::kahan;
     constexpr bool SEL64 = ModeTraits<MODE>::sel64;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const StateView &v = A.v;
-
-    StepOpt<T> O;
-    O.h_frac = (T)A.h_frac;
-    O.h_min = (T)A.h_min;
-    O.eps_xi = (T)A.eps_xi;
+    StepOpt<float> O;
+    O.h_frac = (float)A.h_frac;
+    O.h_min = (float)A.h_min;
+    O.eps_xi = (float)A.eps_xi;
     O.step_rule = A.step_rule;
-    StepOpt<double> O64;
-    O64.h_frac = A.h_frac;
-    O64.h_min = A.h_min;
-    O64.eps_xi = A.eps_xi;
-    O64.step_rule = A.step_rule;
 
-    bool has = false;
-    bool exhausted = false;
+    bool has = false, exhausted = false;
     int64_t id = 0;
-    T y[8], c[8], fin[4];
-    Hole<T> H;
-    Hole<double> H64;
-    int steps = 0, euler = 0, remaps = 0, n64 = 0;
-    int64_t call_steps = 0;
-    unsigned long long tot_steps = 0, tot_euler = 0, tot_fp64 = 0, tot_active = 0;
+    float y[8], c[8], fin[4];
+    Hole<float> H;
+    float r_promote = -INFINITY;
+    int steps = 0, euler = 0, remaps = 0, n64 = 0, used = 0;
+    unsigned long long tot_steps = 0, tot_euler = 0;
 
     for (;;) {
         // ---- refill idle lanes from the work queue (warp-uniform loop) ----
@@ -442,41 +466,49 @@ template <int MODE> __global__ void trace_kernel(TraceArgs A)
             if (lane == leader)
                 base = atomicAdd(&A.ws->head, (unsigned long long)cnt);
             base = __shfl_sync(FULL, base, leader);
+            bool handoff_now = false;
             if (!has) {
-                const int rank = __popc(idle & ((1u << lane) - 1u));
-                const int64_t my = (int64_t)base + rank;
+                const int64_t my = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
                 if (my < A.n) {
                     const int4 s0 = v.S0[my];
                     if (s0.x == GRAY_RAY_ACTIVE) {
-                        has = true;
-                        id = my;
-                        steps = s0.y;
-                        euler = s0.z;
-                        remaps = s0.w;
-                        n64 = v.S1[my];
-                        call_steps = 0;
-                        const d4 p = ld_d4(v.P, my);
-                        H64 = make_hole(p.x, p.y, p.z, A.cap_frac, A.r_esc_frac, A.r_sw);
-                        H = cast_hole<T>(H64);
-                        if (MODE == GRAY_FP64) {
-                            const d4 X = ld_d4(v.X, my), K = ld_d4(v.K, my);
-                            y[0] = (T)X.x; y[1] = (T)X.y; y[2] = (T)X.z; y[3] = (T)X.w;
-                            y[4] = (T)K.x; y[5] = (T)K.y; y[6] = (T)K.z; y[7] = (T)K.w;
+                        const int4 s1 = v.S1[my];
+                        if (SEL64 && (s1.w & FLAG_DOUBLE_MODE)) {
+                            handoff_now = true; // resumed inside the double zone
+                            id = my;
                         } else {
+                            has = true;
+                            id = my;
+                            steps = s0.y;
+                            euler = s0.z;
+                            remaps = s0.w;
+                            n64 = s1.x;
+                            used = (s1.y == A.epoch) ? s1.z : 0;
+                            const d4 p = ld_d4(v.P, my);
+                            const Hole<double> H64 = make_hole(p.x, p.y, p.z, A.cap_frac, A.r_esc_frac, A.r_sw);
+                            H = cast_hole<float>(H64);
+                            r_promote = (float)H64.r_promote;
                             const float4 X = ld_f4(v.X, my), K = ld_f4(v.K, my);
-                            y[0] = (T)X.x; y[1] = (T)X.y; y[2] = (T)X.z; y[3] = (T)X.w;
-                            y[4] = (T)K.x; y[5] = (T)K.y; y[6] = (T)K.z; y[7] = (T)K.w;
+                            y[0] = X.x; y[1] = X.y; y[2] = X.z; y[3] = X.w;
+                            y[4] = K.x; y[5] = K.y; y[6] = K.z; y[7] = K.w;
                             if (KAHAN) {
                                 const float4 CX = ld_f4(v.CX, my), CK = ld_f4(v.CK, my);
                                 c[0] = CX.x; c[1] = CX.y; c[2] = CX.z; c[3] = CX.w;
                                 c[4] = CK.x; c[5] = CK.y; c[6] = CK.z; c[7] = CK.w;
+                            } else {
+#pragma unroll
+                                for (int m = 0; m < 8; ++m)
+                                    c[m] = 0.0f;
                             }
                         }
-                        if (!KAHAN)
-                            for (int m = 0; m < 8; ++m)
-                                c[m] = T(0);
                     }
                 }
+            }
+            if (SEL64) {
+                int rank;
+                const unsigned long long hb = warp_count(&A.ws->handoff, handoff_now, lane, &rank);
+                if (handoff_now)
+                    v.L[hb + rank] = (int)id;
             }
             if ((int64_t)base + cnt >= A.n)
                 exhausted = true;
@@ -486,6 +518,7 @@ template <int MODE> __global__ void trace_kernel(TraceArgs A)
 
         // ---- step block: `refill` steps, then look for idle lanes again ----
         for (int k = 0; k < A.refill; ++k) {
+            bool handoff = false;
             if (has) {
                 int status = GRAY_RAY_ACTIVE;
                 bool yield = false;
@@ -493,71 +526,203 @@ template <int MODE> __global__ void trace_kernel(TraceArgs A)
                     status = GRAY_RAY_STEP_CAP;
                     for (int m = 0; m < 4; ++m)
                         fin[m] = y[m];
-                } else if (A.budget > 0 && call_steps >= A.budget) {
+                } else if (A.budget > 0 && used >= A.budget) {
                     yield = true;
+                } else if (SEL64 && y[1] - c[1] < r_promote) {
+                    handoff = true;
                 } else {
                     const int e0 = euler;
-                    bool promoted = false;
-                    if constexpr (SEL64) {
-                        if ((double)y[1] - (double)c[1] < H64.r_promote) {
-                            status = step_promoted(&H64, &O64, y, c, fin, &euler, &remaps);
-                            promoted = true;
-                            ++n64;
-                            ++tot_fp64;
-                        }
-                    }
-                    if (!promoted)
-                        status = step_once<T, KAHAN>(H, O, y, c, fin, euler, remaps);
+                    status = step_once<float, KAHAN>(H, O, y, c, fin, euler, remaps);
                     tot_euler += (unsigned long long)(euler - e0);
                     ++steps;
-                    ++call_steps;
+                    ++used;
                     ++tot_steps;
                 }
-                if (status != GRAY_RAY_ACTIVE || yield) {
-                    // write the ray back
-                    if (MODE == GRAY_FP64) {
+                if (status != GRAY_RAY_ACTIVE || yield || handoff) {
+                    st_f4(v.X, id, y[0], y[1], y[2], y[3]);
+                    st_f4(v.K, id, y[4], y[5], y[6], y[7]);
+                    if (KAHAN) {
+                        st_f4(v.CX, id, c[0], c[1], c[2], c[3]);
+                        st_f4(v.CK, id, c[4], c[5], c[6], c[7]);
+                    }
+                    if (status != GRAY_RAY_ACTIVE)
+                        st_f4(v.F, id, fin[0], fin[1], fin[2], fin[3]);
+                    v.S0[id] = make_int4(status, steps, euler, remaps);
+                    v.S1[id] = make_int4(n64, A.epoch, used, handoff ? FLAG_DOUBLE_MODE : 0);
+                    has = false;
+                }
+            }
+            if (SEL64) {
+                int rank;
+                const unsigned long long hb = warp_count(&A.ws->handoff, handoff, lane, &rank);
+                if (handoff)
+                    v.L[hb + rank] = (int)id;
+            }
+        }
+    }
+    warp_stats<float>(A, lane, tot_steps, tot_euler, 0ull);
+}
+
+// Double-precision persistent tracer.  LIST = false: every ray of a GRAY_FP64
+// buffer.  LIST = true: the rays of the hand-off list of a
+// GRAY_FP32_KAHAN_SEL64 buffer (states in its single-precision planes).
+template <bool LIST> __global__ void __launch_bounds__(128) trace64_kernel(TraceArgs A)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const StateView &v = A.v;
+    StepOpt<double> O;
+    O.h_frac = A.h_frac;
+    O.h_min = A.h_min;
+    O.eps_xi = A.eps_xi;
+    O.step_rule = A.step_rule;
+    const int64_t n = LIST ? (int64_t)*(volatile unsigned long long *)&A.ws->handoff : A.n;
+
+    bool has = false, exhausted = false;
+    int64_t id = 0;
+    double y[8], cz[8], fin[4];
+    Hole<double> H;
+    double r_demote = INFINITY;
+    int steps = 0, euler = 0, remaps = 0, n64 = 0, used = 0;
+    unsigned long long tot_steps = 0, tot_euler = 0, tot_fp64 = 0;
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+        cz[m] = 0.0;
+
+    for (;;) {
+        while (!exhausted) {
+            const unsigned idle = __ballot_sync(FULL, !has);
+            if (idle == 0)
+                break;
+            const int cnt = __popc(idle);
+            const int leader = __ffs(idle) - 1;
+            unsigned long long base = 0;
+            if (lane == leader)
+                base = atomicAdd(&A.ws->head, (unsigned long long)cnt);
+            base = __shfl_sync(FULL, base, leader);
+            if (!has) {
+                const int64_t slot = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
+                if (slot < n) {
+                    const int64_t my = LIST ? (int64_t)v.L[slot] : slot;
+                    const int4 s0 = v.S0[my];
+                    if (s0.x == GRAY_RAY_ACTIVE) {
+                        const int4 s1 = v.S1[my];
+                        has = true;
+                        id = my;
+                        steps = s0.y;
+                        euler = s0.z;
+                        remaps = s0.w;
+                        n64 = s1.x;
+                        used = (s1.y == A.epoch) ? s1.z : 0;
+                        const d4 p = ld_d4(v.P, my);
+                        H = make_hole(p.x, p.y, p.z, A.cap_frac, A.r_esc_frac, A.r_sw);
+                        r_demote = H.r_promote + A.r_sw;
+                        if (!LIST) {
+                            const d4 X = ld_d4(v.X, my), K = ld_d4(v.K, my);
+                            y[0] = X.x; y[1] = X.y; y[2] = X.z; y[3] = X.w;
+                            y[4] = K.x; y[5] = K.y; y[6] = K.z; y[7] = K.w;
+                        } else if (s1.w & FLAG_DOUBLE_REPR) {
+                            // exact double state parked in the four single planes
+                            const double2 q0 = ((const double2 *)v.X)[my], q1 = ((const double2 *)v.K)[my];
+                            const double2 q2 = ((const double2 *)v.CX)[my], q3 = ((const double2 *)v.CK)[my];
+                            y[0] = q0.x; y[1] = q0.y; y[2] = q1.x; y[3] = q1.y;
+                            y[4] = q2.x; y[5] = q2.y; y[6] = q3.x; y[7] = q3.y;
+                        } else {
+                            const float4 X = ld_f4(v.X, my), K = ld_f4(v.K, my);
+                            const float4 CX = ld_f4(v.CX, my), CK = ld_f4(v.CK, my);
+                            y[0] = (double)X.x - CX.x; y[1] = (double)X.y - CX.y;
+                            y[2] = (double)X.z - CX.z; y[3] = (double)X.w - CX.w;
+                            y[4] = (double)K.x - CK.x; y[5] = (double)K.y - CK.y;
+                            y[6] = (double)K.z - CK.z; y[7] = (double)K.w - CK.w;
+                        }
+                    }
+                }
+            }
+            if ((int64_t)base + cnt >= n)
+                exhausted = true;
+        }
+        if (!__any_sync(FULL, has))
+            break;
+
+        for (int k = 0; k < A.refill; ++k) {
+            bool demote = false;
+            if (has) {
+                int status = GRAY_RAY_ACTIVE;
+                bool yield = false;
+                if (steps >= A.max_steps) {
+                    status = GRAY_RAY_STEP_CAP;
+                    for (int m = 0; m < 4; ++m)
+                        fin[m] = y[m];
+                } else if (A.budget > 0 && used >= A.budget) {
+                    yield = true;
+                } else if (LIST && y[1] >= r_demote) {
+                    demote = true;
+                } else {
+                    const int e0 = euler;
+                    status = step_once<double, false>(H, O, y, cz, fin, euler, remaps);
+                    tot_euler += (unsigned long long)(euler - e0);
+                    ++steps;
+                    ++used;
+                    ++tot_steps;
+                    if (LIST) {
+                        ++n64;
+                        ++tot_fp64;
+                    }
+                }
+                if (status != GRAY_RAY_ACTIVE || yield || demote) {
+                    int flags = 0;
+                    if (!LIST) {
                         st_d4(v.X, id, y[0], y[1], y[2], y[3]);
                         st_d4(v.K, id, y[4], y[5], y[6], y[7]);
                         if (status != GRAY_RAY_ACTIVE)
                             st_d4(v.F, id, fin[0], fin[1], fin[2], fin[3]);
+                    } else if (yield) {
+                        // park the exact double state; the ray resumes in double
+                        ((double2 *)v.X)[id] = make_double2(y[0], y[1]);
+                        ((double2 *)v.K)[id] = make_double2(y[2], y[3]);
+                        ((double2 *)v.CX)[id] = make_double2(y[4], y[5]);
+                        ((double2 *)v.CK)[id] = make_double2(y[6], y[7]);
+                        flags = FLAG_DOUBLE_MODE | FLAG_DOUBLE_REPR;
                     } else {
-                        st_f4(v.X, id, (float)y[0], (float)y[1], (float)y[2], (float)y[3]);
-                        st_f4(v.K, id, (float)y[4], (float)y[5], (float)y[6], (float)y[7]);
-                        if (KAHAN) {
-                            st_f4(v.CX, id, (float)c[0], (float)c[1], (float)c[2], (float)c[3]);
-                            st_f4(v.CK, id, (float)c[4], (float)c[5], (float)c[6], (float)c[7]);
+                        // back to a compensated single-precision pair (hi, hi - y)
+                        float hi[8], lo[8];
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) {
+                            hi[m] = (float)y[m];
+                            lo[m] = (float)((double)hi[m] - y[m]);
                         }
+                        st_f4(v.X, id, hi[0], hi[1], hi[2], hi[3]);
+                        st_f4(v.K, id, hi[4], hi[5], hi[6], hi[7]);
+                        st_f4(v.CX, id, lo[0], lo[1], lo[2], lo[3]);
+                        st_f4(v.CK, id, lo[4], lo[5], lo[6], lo[7]);
                         if (status != GRAY_RAY_ACTIVE)
                             st_f4(v.F, id, (float)fin[0], (float)fin[1], (float)fin[2], (float)fin[3]);
                     }
                     v.S0[id] = make_int4(status, steps, euler, remaps);
-                    v.S1[id] = n64;
-                    if (yield)
-                        ++tot_active;
+                    v.S1[id] = make_int4(n64, A.epoch, used, flags);
                     has = false;
                 }
             }
+            if (LIST) {
+                int rank;
+                (void)warp_count(&A.ws->demoted, demote, lane, &rank);
+            }
         }
     }
+    warp_stats<double>(A, lane, tot_steps, tot_euler, tot_fp64);
+}
 
-    // ---- per-call statistics: one atomic per warp per counter ----
+// Rays still ACTIVE (for the per-call statistics).
+__global__ void count_active_kernel(const int4 *S0, int64_t n, unsigned long long *out)
+{
+    unsigned long long mine = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        mine += (S0[i].x == GRAY_RAY_ACTIVE);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        tot_steps += __shfl_xor_sync(FULL, tot_steps, off);
-        tot_euler += __shfl_xor_sync(FULL, tot_euler, off);
-        tot_fp64 += __shfl_xor_sync(FULL, tot_fp64, off);
-        tot_active += __shfl_xor_sync(FULL, tot_active, off);
-    }
-    if (lane == 0) {
-        if (tot_steps)
-            atomicAdd(&A.ws->steps, tot_steps);
-        if (tot_euler)
-            atomicAdd(&A.ws->euler, tot_euler);
-        if (tot_fp64)
-            atomicAdd(&A.ws->fp64, tot_fp64);
-        if (tot_active)
-            atomicAdd(&A.ws->active, tot_active);
-    }
+    for (int off = 16; off > 0; off >>= 1)
+        mine += __shfl_xor_sync(0xffffffffu, mine, off);
+    if ((threadIdx.x & 31) == 0 && mine)
+        atomicAdd(out, mine);
 }
 
 // --------------------------------------------------------------------------
@@ -573,6 +738,14 @@ __device__ void load_state_double(const StateView &v, int prec, int64_t i, doubl
         fin[0] = F.x; fin[1] = F.y; fin[2] = F.z; fin[3] = F.w;
     } else {
         const float4 X = ld_f4(v.X, i), K = ld_f4(v.K, i), F = ld_f4(v.F, i);
+        fin[0] = F.x; fin[1] = F.y; fin[2] = F.z; fin[3] = F.w;
+        if (prec == GRAY_FP32_KAHAN_SEL64 && (v.S1[i].w & FLAG_DOUBLE_REPR)) {
+            const double2 q0 = ((const double2 *)v.X)[i], q1 = ((const double2 *)v.K)[i];
+            const double2 q2 = ((const double2 *)v.CX)[i], q3 = ((const double2 *)v.CK)[i];
+            y[0] = q0.x; y[1] = q0.y; y[2] = q1.x; y[3] = q1.y;
+            y[4] = q2.x; y[5] = q2.y; y[6] = q3.x; y[7] = q3.y;
+            return;
+        }
         float4 CX = make_float4(0, 0, 0, 0), CK = CX;
         if (prec != GRAY_FP32) {
             CX = ld_f4(v.CX, i);
@@ -618,7 +791,7 @@ __global__ void render_kernel(StateView v, int prec, int64_t first, int64_t n, i
             o[4 + m] = fin[m];
         for (int m = 0; m < 8; ++m)
             o[8 + m] = y[m];
-        o[16] = v.S1[i];
+        o[16] = v.S1[i].x;
     } else { // GRAY_RENDER_INVARIANTS, in double from the stored state
         const d4 p = ld_d4(v.P, i);
         const Hole<double> H = make_hole(p.x, p.y, p.z, 1.0, 1.0, 0.0);
@@ -965,67 +1138,93 @@ int gray_trace(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, 
     if (cudaMemsetAsync(ctx->ws, 0, sizeof(Workspace), s) != cudaSuccess)
         return GRAY_ECUDA;
     const gray_options &o = ctx->opt;
-    if (n_state > 0) {
-        TraceArgs A;
-        A.v = make_view(state, n_state, o.precision);
-        A.n = n_state;
-        A.budget = step_budget;
-        A.max_steps = o.max_steps;
-        A.refill = o.refill > 0 ? o.refill : 8;
-        A.h_frac = o.h_frac;
-        A.h_min = o.h_min;
-        A.eps_xi = o.eps_xi;
-        A.cap_frac = o.cap_frac;
-        A.r_esc_frac = o.r_esc_frac;
-        A.r_sw = o.r_sw;
-        A.step_rule = o.step_rule;
-        A.ws = ctx->ws;
-        const int block = o.block > 0 ? o.block : 128;
+    ctx->epoch = ctx->epoch == 0x7fffffff ? 1 : ctx->epoch + 1;
+    TraceArgs A;
+    A.v = make_view(state, n_state, o.precision);
+    A.n = n_state;
+    A.budget = step_budget;
+    A.max_steps = o.max_steps;
+    A.refill = o.refill > 0 ? o.refill : 8;
+    A.step_rule = o.step_rule;
+    A.epoch = ctx->epoch;
+    A.h_frac = o.h_frac;
+    A.h_min = o.h_min;
+    A.eps_xi = o.eps_xi;
+    A.cap_frac = o.cap_frac;
+    A.r_esc_frac = o.r_esc_frac;
+    A.r_sw = o.r_sw;
+    A.ws = ctx->ws;
+    const int block = o.block > 0 ? o.block : 128;
+    // persistent grid: resident blocks per SM x SMs, never more blocks than work
+    auto grid_of = [&](const void *kernel, int64_t work) -> unsigned {
         int per_sm = o.blocks_per_sm;
         if (per_sm <= 0) {
             per_sm = 1;
-            switch (o.precision) {
-            case GRAY_FP64:
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<GRAY_FP64>, block, 0);
-                break;
-            case GRAY_FP32:
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<GRAY_FP32>, block, 0);
-                break;
-            case GRAY_FP32_KAHAN:
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<GRAY_FP32_KAHAN>, block, 0);
-                break;
-            default:
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trace_kernel<GRAY_FP32_KAHAN_SEL64>, block,
-                                                              0);
-                break;
-            }
-            if (per_sm < 1)
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1)
                 per_sm = 1;
         }
         int64_t want = (int64_t)per_sm * ctx->num_sms;
-        const int64_t need = (n_state + block - 1) / block;
+        const int64_t need = (work + block - 1) / block;
         if (want > need)
             want = need;
-        const unsigned grid = (unsigned)(want > 0 ? want : 1);
+        return (unsigned)(want > 0 ? want : 1);
+    };
+    const bool sel64 = o.precision == GRAY_FP32_KAHAN_SEL64;
+    if (n_state > 0) {
         switch (o.precision) {
         case GRAY_FP64:
-            trace_kernel<GRAY_FP64><<<grid, block, 0, s>>>(A);
+            trace64_kernel<false><<<grid_of((const void *)trace64_kernel<false>, n_state), block, 0, s>>>(A);
             break;
         case GRAY_FP32:
-            trace_kernel<GRAY_FP32><<<grid, block, 0, s>>>(A);
+            trace32_kernel<GRAY_FP32><<<grid_of((const void *)trace32_kernel<GRAY_FP32>, n_state), block, 0, s>>>(A);
             break;
         case GRAY_FP32_KAHAN:
-            trace_kernel<GRAY_FP32_KAHAN><<<grid, block, 0, s>>>(A);
+            trace32_kernel<GRAY_FP32_KAHAN>
+                <<<grid_of((const void *)trace32_kernel<GRAY_FP32_KAHAN>, n_state), block, 0, s>>>(A);
             break;
         default:
-            trace_kernel<GRAY_FP32_KAHAN_SEL64><<<grid, block, 0, s>>>(A);
             break;
         }
-        if ((rc = check_launch()))
+        if (!sel64 && (rc = check_launch()))
             return rc;
+        // Selective double: alternate a single-precision pass over the buffer
+        // and a double-precision pass over the hand-off list until no ray is
+        // handed off or returned; the host reads two counters between passes.
+        const unsigned g32 = grid_of((const void *)trace32_kernel<GRAY_FP32_KAHAN_SEL64>, n_state);
+        for (int round = 0; sel64 && round < 1000; ++round) {
+            trace32_kernel<GRAY_FP32_KAHAN_SEL64><<<g32, block, 0, s>>>(A);
+            if ((rc = check_launch()))
+                return rc;
+            if (cudaMemcpyAsync(ctx->ws_host, ctx->ws, sizeof(Workspace), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return GRAY_ECUDA;
+            const unsigned long long handed = ctx->ws_host->handoff;
+            if (handed == 0)
+                break;
+            if (cudaMemsetAsync(&ctx->ws->head, 0, sizeof(unsigned long long), s) != cudaSuccess)
+                return GRAY_ECUDA;
+            trace64_kernel<true><<<grid_of((const void *)trace64_kernel<true>, (int64_t)handed), block, 0, s>>>(A);
+            if ((rc = check_launch()))
+                return rc;
+            if (cudaMemcpyAsync(ctx->ws_host, ctx->ws, sizeof(Workspace), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return GRAY_ECUDA;
+            if (ctx->ws_host->demoted == 0)
+                break;
+            // next round: fresh queue, empty hand-off list
+            if (cudaMemsetAsync(&ctx->ws->head, 0, sizeof(unsigned long long), s) != cudaSuccess ||
+                cudaMemsetAsync(&ctx->ws->handoff, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess)
+                return GRAY_ECUDA;
+        }
     }
     if (!n_active_host && !stats_host)
         return 1;
+    if (n_state > 0) {
+        count_active_kernel<<<grid_for(n_state, 256) < 1024 ? grid_for(n_state, 256) : 1024, 256, 0, s>>>(
+            A.v.S0, n_state, &ctx->ws->active);
+        if ((rc = check_launch()))
+            return rc;
+    }
     if (cudaMemcpyAsync(ctx->ws_host, ctx->ws, sizeof(Workspace), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return GRAY_ECUDA;

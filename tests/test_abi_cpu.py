@@ -37,7 +37,7 @@ def test_state_bytes(L):
         b1 = gray.gray_state_bytes(1, prec)
         assert b1 > 0 and b1 % 256 == 0
         n = 1 << 20
-        per = (32 * 3 if prec == gray.FP64 else 16 * 5) + 32 + 16 + 4
+        per = (32 * 3 if prec == gray.FP64 else 16 * 5) + 32 + 16 + 16 + 4
         assert gray.gray_state_bytes(n, prec) == per * n
     assert gray.gray_state_bytes(-1, gray.FP64) == 0
     assert gray.gray_state_bytes(10, 7) == 0
