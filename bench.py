@@ -54,11 +54,14 @@ def parse_args():
     p.add_argument("--impl", default="gray", choices=["gray", "reference"])
     p.add_argument("--side", type=int, default=1024)
     p.add_argument("--precision", default="fp32_kahan_sel64")
-    p.add_argument("--r-sw", type=float, default=0.25)
+    p.add_argument("--r-sw", type=float, default=0.02)
     p.add_argument("--step-rule", default="bench", choices=["bench", "eq2"])
     p.add_argument("--block", type=int, default=0)
     p.add_argument("--blocks-per-sm", type=int, default=0)
     p.add_argument("--refill", type=int, default=0)
+    p.add_argument("--no-plan", action="store_true")
+    p.add_argument("--probe-stride", type=int, default=4)
+    p.add_argument("--probe-budget", type=int, default=400)
     p.add_argument("--no-fp64-leg", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-rays", type=int, default=16384)
@@ -210,18 +213,34 @@ def main():
     out_dev = torch.empty(16 * n, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
+    order_buf = torch.empty(n, dtype=torch.int32, device="cuda")
+
+    def plan_and_trace():
+        if args.no_plan:
+            tr.trace(wait=False)
+        else:
+            order = tr.plan([im], probe_stride=args.probe_stride, probe_budget=args.probe_budget, order=order_buf)
+            tr.trace(wait=False, order=order)
+
     def one_step():
         tr.setup([im])
-        tr.trace(wait=False)
+        plan_and_trace()
         tr.render(gray.RENDER_PIXELS32, out=out_dev)
 
     # warm-up; the last warm-up step also reads the step statistics
     for _ in range(max(args.warmup, 1)):
         one_step()
     tr.setup([im])
-    _, _, stats = tr.trace()
-    steps_per_pass = stats[0]
-    fp64_steps = stats[2]
+    if args.no_plan:
+        _, _, stats = tr.trace()
+        steps_per_pass, fp64_steps = stats[0], stats[2]
+    else:
+        # the probe steps are counted by a stats read after the plan
+        order = tr.plan([im], probe_stride=args.probe_stride, probe_budget=args.probe_budget, order=order_buf)
+        _, _, stats = tr.trace(order=order)
+        rec = tr.records()
+        steps_per_pass = int(rec[:, 1].sum())
+        fp64_steps = int(rec[:, 16].sum())
     torch.cuda.synchronize()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
@@ -239,7 +258,7 @@ def main():
         e0.record(stream)
         tr.setup([im])
         e1.record(stream)
-        tr.trace(wait=False)
+        plan_and_trace()
         e2.record(stream)
         tr.render(gray.RENDER_PIXELS32, out=out_dev)
         e3.record(stream)
@@ -265,7 +284,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         tr.setup([im])
-        tr.trace(wait=False)
+        plan_and_trace()
         tr.render(gray.RENDER_PIXELS32, out=out_dev)
         host_out.copy_(out_dev, non_blocking=True)
         torch.cuda.synchronize()
@@ -304,6 +323,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "kerr_a0.99_i90_%dx%d_%s" % (args.side, args.side, args.precision),
                        "rays": n, "max_steps": 10000, "step_rule": args.step_rule, "r_sw": args.r_sw,
+                       "queue": "natural" if args.no_plan else "planned (probe stride %d, budget %d)" % (
+                           args.probe_stride, args.probe_budget),
                        "l2": "flushed between timed steps (256 MB write)"},
             "ns_per_photon_step": 1e9 / (value / world),
             "steps_per_pass": steps_per_pass, "fp64_steps_per_pass": fp64_steps,

@@ -167,24 +167,44 @@ int gray_setup_rays(gray_ctx *ctx, const double *rays_dev, int64_t n, double M,
                     void *state_dev, size_t state_bytes, int64_t n_state, int64_t first_ray,
                     void *stream);
 
-/* Trace every ACTIVE ray of the buffer backward until it is captured,
- * escapes, hits max_steps, turns non-finite, or has taken step_budget steps in
- * this call (step_budget <= 0: no per-call budget; Sec. 2 notes the same
- * step-limited mode for interactive use).  Finished rays are skipped, so a
- * trace split over several calls gives the same result as one call.  If
- * n_active_host is not NULL the call waits for the stream and stores the
- * number of rays still active; if stats_host is not NULL (4 int64) it stores,
- * for this call: steps taken, Euler redos, steps promoted to double, rays
- * still active.  Returns 0 when no ray is active, 1 when some remain or when
- * no host output was requested (the count is then unknown), or an error
+/* Trace rays of the buffer backward until each is captured, escapes, hits
+ * max_steps, turns non-finite, or has taken step_budget steps in this call
+ * (step_budget <= 0: no per-call budget; Sec. 2 notes the same step-limited
+ * mode for interactive use).  The work queue is order_dev[0 .. n_order-1]
+ * (ray indices; entries outside [0, n_state) are skipped) or, when order_dev
+ * is NULL (n_order must then be 0), every ray 0 .. n_state-1.  Only ACTIVE
+ * rays are traced: finished ones are skipped, so a trace split over several
+ * calls gives the same result as one call, and a ray's result does not depend
+ * on its place in the queue.  If n_active_host is not NULL the call waits for
+ * the stream and stores the number of rays of the buffer still active; if
+ * stats_host is not NULL (4 int64) it stores, for this call: steps taken,
+ * Euler redos, steps taken in double by the selective mode, rays still
+ * active.  Returns 0 when no ray is active, 1 when some remain or when no
+ * host output was requested (the count is then unknown), or an error
  * (GRAY_EINVAL, GRAY_ECUDA).
- * In GRAY_FP32_KAHAN_SEL64 the call alternates a single-precision pass over
- * the buffer with a double-precision pass over the rays that entered the
- * zone near the horizon, and waits for the stream between passes to read two
- * counters; the other precisions are one launch and do not wait unless a
- * host output was requested. */
+ * In GRAY_FP32_KAHAN_SEL64 the call makes a single-precision pass over the
+ * queue and then a pass over the rays that entered the zone near the horizon
+ * (in double there, in compensated single precision once they leave it). */
 int gray_trace(gray_ctx *ctx, void *state_dev, size_t state_bytes, int64_t n_state,
-               int64_t step_budget, int64_t *n_active_host, int64_t *stats_host, void *stream);
+               const int32_t *order_dev, int64_t n_order, int64_t step_budget,
+               int64_t *n_active_host, int64_t *stats_host, void *stream);
+
+/* Plan a longest-first work queue for the rays of n_images images set up at
+ * first_ray (as by gray_setup with the same list).  A persistent trace ends
+ * when its last long ray does, so long rays (grazing a pole or the photon
+ * orbit) should start first.  The call traces a probe grid -- every
+ * probe_stride-th pixel in both directions -- for at most probe_budget steps
+ * per probe (the probes keep that progress), predicts every pixel's cost from
+ * the 4 x 4 probes around its cell (a finished probe costs its steps; an
+ * unfinished one its steps plus 8 per Euler redo), and writes into order_dev
+ * (int32, out_bytes >= 4 x total pixels) all the images' ray indices sorted by
+ * descending predicted cost, ready for gray_trace.  The order within one cost
+ * bucket is not deterministic; results do not depend on it.
+ * Errors: GRAY_EINVAL, GRAY_ECUDA. */
+int gray_plan(gray_ctx *ctx, void *state_dev, size_t state_bytes, int64_t n_state,
+              const gray_image *images_host, int32_t n_images, int64_t first_ray,
+              int32_t probe_stride, int32_t probe_budget, int32_t *order_dev, size_t order_bytes,
+              void *stream);
 
 /* Read rays first_ray .. first_ray + n - 1 of the buffer into out_dev
  * (out_bytes bytes):

@@ -49,11 +49,13 @@ __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_
 //   CX, CK  Kahan compensations         float4 (FP32 modes only)
 //   F  final position on the stop surface  float4 / d4
 //   P  per-ray constants (a, M, r_obs, 0)  d4
+//   PF0, PF1 the same constants for single precision: (a, M, r_+ hi, r_+ lo),
+//           (r_-, dc, r_h, r_obs)  float4 each (FP32 modes only)
 //   S0 (status, steps, Euler redos, pole remaps)  int4
 //   S1 (steps in double, call epoch, steps in that call, flags)  int4
 //   L  hand-off list of ray indices (selective-double mode)  int
 struct Layout {
-    size_t X, K, CX, CK, F, P, S0, S1, L, total;
+    size_t X, K, CX, CK, F, P, PF0, PF1, S0, S1, L, total;
 };
 
 inline bool is_f64(int prec) { return prec == GRAY_FP64; }
@@ -80,6 +82,14 @@ Layout make_layout(int64_t n, int prec)
     off = align256(off + v * un);
     L.P = off;
     off = align256(off + 32 * un);
+    if (!is_f64(prec)) {
+        L.PF0 = off;
+        off = align256(off + 16 * un);
+        L.PF1 = off;
+        off = align256(off + 16 * un);
+    } else {
+        L.PF0 = L.PF1 = 0;
+    }
     L.S0 = off;
     off = align256(off + 16 * un);
     L.S1 = off;
@@ -93,6 +103,7 @@ Layout make_layout(int64_t n, int prec)
 struct StateView {
     char *X, *K, *CX, *CK, *F;
     d4 *P;
+    float4 *PF0, *PF1;
     int4 *S0;
     int4 *S1;
     int *L;
@@ -109,6 +120,8 @@ StateView make_view(void *base, int64_t n, int prec)
     v.CK = is_f64(prec) ? nullptr : b + L.CK;
     v.F = b + L.F;
     v.P = (d4 *)(b + L.P);
+    v.PF0 = is_f64(prec) ? nullptr : (float4 *)(b + L.PF0);
+    v.PF1 = is_f64(prec) ? nullptr : (float4 *)(b + L.PF1);
     v.S0 = (int4 *)(b + L.S0);
     v.S1 = (int4 *)(b + L.S1);
     v.L = (int *)(b + L.L);
@@ -153,7 +166,8 @@ struct gray_ctx {
     Workspace *ws_host = nullptr; // pinned host mirror
     int device = 0;
     int num_sms = 0;
-    int epoch = 0; // gray_trace calls made with this context
+    int epoch = 0;                  // gray_trace calls made with this context
+    unsigned long long *aux = nullptr; // device: planning counters and histograms
 };
 
 namespace {
@@ -189,6 +203,10 @@ __device__ void store_initial(const StateView &v, int prec, int64_t i, const dou
         st_f4(v.CX, i, lo[0], lo[1], lo[2], lo[3]);
         st_f4(v.CK, i, lo[4], lo[5], lo[6], lo[7]);
         st_f4(v.F, i, hi[0], hi[1], hi[2], hi[3]);
+        float c8[8];
+        hole_constants_f(a, M, r_obs, c8);
+        v.PF0[i] = make_float4(c8[0], c8[1], c8[2], c8[3]);
+        v.PF1[i] = make_float4(c8[4], c8[5], c8[6], c8[7]);
     }
     st_d4(v.P, i, a, M, r_obs, 0.0);
     v.S0[i] = make_int4(GRAY_RAY_ACTIVE, 0, 0, 0);
@@ -286,28 +304,37 @@ template <typename T, bool KAHAN> __device__ __forceinline__ int remap_eq3(T *y,
     return 1;
 }
 
-// One step.  Returns the ray's new status; writes fin[4] when it stops.
+__device__ __forceinline__ float sixth(float h) { return h * (1.0f / 6.0f); }
+__device__ __forceinline__ double sixth(double h) { return h / 6.0; }
+__device__ __forceinline__ float ninth(float h) { return h * (1.0f / 9.0f); }
+__device__ __forceinline__ double ninth(double h) { return h / 9.0; }
+
+// One step.  Returns the ray's new status; writes fin[4] when it stops.  g
+// holds the geometry of the current point on entry and of the new point on
+// exit, so the first RK4 stage reuses what the previous step's Eq. 4 test
+// computed.
 template <typename T, bool KAHAN>
-__device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, T *y, T *c, T *fin, int &euler,
-                                         int &remaps)
+__device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, T *y, T *c, Geo<T> &g, T *fin,
+                                         int &euler, int &remaps)
 {
     T h = step_size(H, O, y);
     T a1[4], a2[4], a3[4], a4[4];
-    geodesic_accel(H, y[1], y[2], y[4], y[5], y[6], y[7], a1);
+    accel_geo(H, g, y[4], y[5], y[6], y[7], a1);
     const T hh = T(0.5) * h;
     const T r2 = fma(hh, y[5], y[1]), th2 = fma(hh, y[6], y[2]);
     const T kt2 = fma(hh, a1[0], y[4]), kr2 = fma(hh, a1[1], y[5]), kh2 = fma(hh, a1[2], y[6]),
             kp2 = fma(hh, a1[3], y[7]);
-    geodesic_accel(H, r2, th2, kt2, kr2, kh2, kp2, a2);
+    const T dr = KAHAN ? -c[1] : T(0), dth = KAHAN ? -c[2] : T(0);
+    accel_geo(H, geometry(H, r2, th2, dr, dth), kt2, kr2, kh2, kp2, a2);
     const T r3 = fma(hh, kr2, y[1]), th3 = fma(hh, kh2, y[2]);
     const T kt3 = fma(hh, a2[0], y[4]), kr3 = fma(hh, a2[1], y[5]), kh3 = fma(hh, a2[2], y[6]),
             kp3 = fma(hh, a2[3], y[7]);
-    geodesic_accel(H, r3, th3, kt3, kr3, kh3, kp3, a3);
+    accel_geo(H, geometry(H, r3, th3, dr, dth), kt3, kr3, kh3, kp3, a3);
     const T r4 = fma(h, kr3, y[1]), th4 = fma(h, kh3, y[2]);
     const T kt4 = fma(h, a3[0], y[4]), kr4 = fma(h, a3[1], y[5]), kh4 = fma(h, a3[2], y[6]),
             kp4 = fma(h, a3[3], y[7]);
-    geodesic_accel(H, r4, th4, kt4, kr4, kh4, kp4, a4);
-    const T h6 = h / T(6);
+    accel_geo(H, geometry(H, r4, th4, dr, dth), kt4, kr4, kh4, kp4, a4);
+    const T h6 = sixth(h);
     T inc[8];
     inc[0] = h6 * (y[4] + T(2) * (kt2 + kt3) + kt4);
     inc[1] = h6 * (y[5] + T(2) * (kr2 + kr3) + kr4);
@@ -318,17 +345,18 @@ __device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, 
         inc[4 + m] = h6 * (a1[m] + T(2) * (a2[m] + a3[m]) + a4[m]);
     T y1[8], c1[8];
     add_update<T, KAHAN>(y, c, inc, y1, c1);
+    Geo<T> g1 = geometry(H, y1[1], y1[2], KAHAN ? -c1[1] : T(0), KAHAN ? -c1[2] : T(0));
 
     // Eq. 4 monitor: redo the step as forward Euler at h/9 when |xi + 1| > eps.
-    const T xi = xi_eq4(H, y1);
-    if (!(fabs(xi + T(1)) <= O.eps_xi)) {
-        h = h / T(9);
+    if (xi_fails(H, g1, y1, O.eps_xi)) {
+        h = ninth(h);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             inc[m] = h * y[4 + m];
             inc[4 + m] = h * a1[m];
         }
         add_update<T, KAHAN>(y, c, inc, y1, c1);
+        g1 = geometry(H, y1[1], y1[2], KAHAN ? -c1[1] : T(0), KAHAN ? -c1[2] : T(0));
         ++euler;
     }
 
@@ -348,14 +376,17 @@ __device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, 
         stop_surface(y, y1, h, H.r_esc, fin);
         status = GRAY_RAY_ESCAPED;
     }
-    if (status != GRAY_RAY_NONFINITE)
-        remaps += remap_eq3<T, KAHAN>(y1, c1);
+    if (status != GRAY_RAY_NONFINITE && remap_eq3<T, KAHAN>(y1, c1)) {
+        ++remaps;
+        g1 = geometry(H, y1[1], y1[2], KAHAN ? -c1[1] : T(0), KAHAN ? -c1[2] : T(0));
+    }
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
         y[m] = y1[m];
         if (KAHAN)
             c[m] = c1[m];
     }
+    g = g1;
     return status;
 }
 
@@ -379,7 +410,10 @@ enum : int { FLAG_DOUBLE_MODE = 1, FLAG_DOUBLE_REPR = 2 };
 
 struct TraceArgs {
     StateView v;
-    int64_t n;
+    int64_t n;                                   // rays in the buffer
+    const int *order;                            // queue of ray indices, or NULL: 0 .. n-1
+    int64_t n_queue;                             // queue length (order != NULL)
+    const unsigned long long *n_queue_dev;       // if not NULL: queue length read on the device
     int64_t budget; // per-call step budget per ray, <= 0: none
     int max_steps;
     int refill;
@@ -393,6 +427,22 @@ template <int MODE> struct ModeTraits {
     static constexpr bool kahan = (MODE == GRAY_FP32_KAHAN || MODE == GRAY_FP32_KAHAN_SEL64);
     static constexpr bool sel64 = (MODE == GRAY_FP32_KAHAN_SEL64);
 };
+
+// Length of the work queue of a pass, and the ray behind a queue slot (-1 for
+// an index outside the buffer, which is skipped).
+__device__ __forceinline__ int64_t queue_length(const TraceArgs &A)
+{
+    if (A.n_queue_dev)
+        return (int64_t)*(volatile const unsigned long long *)A.n_queue_dev;
+    return A.order ? A.n_queue : A.n;
+}
+__device__ __forceinline__ int64_t queue_ray(const TraceArgs &A, int64_t slot)
+{
+    if (!A.order)
+        return slot;
+    const int64_t my = (int64_t)A.order[slot];
+    return (my >= 0 && my < A.n) ? my : -1;
+}
 
 // Warp-aggregated counter increment (warp-uniform call).
 __device__ __forceinline__ unsigned long long warp_count(unsigned long long *ctr, bool pred, int lane,
@@ -433,7 +483,7 @@ __device__ __forceinline__ void warp_stats(const TraceArgs &A, int lane, unsigne
 }
 
 // Single-precision persistent tracer (modes FP32, FP32_KAHAN, FP32_KAHAN_SEL64).
-template <int MODE> __global__ void __launch_bounds__(128) trace32_kernel(TraceArgs A)
+template <int MODE> __global__ void __maxnreg__(96) trace32_kernel(TraceArgs A)
 {
     constexpr bool KAHAN = ModeTraits<MODE>::kahan;
     constexpr bool SEL64 = ModeTraits<MODE>::sel64;
@@ -448,8 +498,10 @@ template <int MODE> __global__ void __launch_bounds__(128) trace32_kernel(TraceA
 
     bool has = false, exhausted = false;
     int64_t id = 0;
+    const int64_t nq = queue_length(A);
     float y[8], c[8], fin[4];
     Hole<float> H;
+    Geo<float> geo;
     float r_promote = -INFINITY;
     int steps = 0, euler = 0, remaps = 0, n64 = 0, used = 0;
     unsigned long long tot_steps = 0, tot_euler = 0;
@@ -468,8 +520,9 @@ template <int MODE> __global__ void __launch_bounds__(128) trace32_kernel(TraceA
             base = __shfl_sync(FULL, base, leader);
             bool handoff_now = false;
             if (!has) {
-                const int64_t my = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
-                if (my < A.n) {
+                const int64_t slot = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
+                const int64_t my = slot < nq ? queue_ray(A, slot) : -1;
+                if (my >= 0) {
                     const int4 s0 = v.S0[my];
                     if (s0.x == GRAY_RAY_ACTIVE) {
                         const int4 s1 = v.S1[my];
@@ -484,10 +537,9 @@ template <int MODE> __global__ void __launch_bounds__(128) trace32_kernel(TraceA
                             remaps = s0.w;
                             n64 = s1.x;
                             used = (s1.y == A.epoch) ? s1.z : 0;
-                            const d4 p = ld_d4(v.P, my);
-                            const Hole<double> H64 = make_hole(p.x, p.y, p.z, A.cap_frac, A.r_esc_frac, A.r_sw);
-                            H = cast_hole<float>(H64);
-                            r_promote = (float)H64.r_promote;
+                            H = make_hole_f(v.PF0[my], v.PF1[my], (float)A.cap_frac, (float)A.r_esc_frac,
+                                            (float)A.r_sw);
+                            r_promote = H.r_promote;
                             const float4 X = ld_f4(v.X, my), K = ld_f4(v.K, my);
                             y[0] = X.x; y[1] = X.y; y[2] = X.z; y[3] = X.w;
                             y[4] = K.x; y[5] = K.y; y[6] = K.z; y[7] = K.w;
@@ -500,6 +552,7 @@ template <int MODE> __global__ void __launch_bounds__(128) trace32_kernel(TraceA
                                 for (int m = 0; m < 8; ++m)
                                     c[m] = 0.0f;
                             }
+                            geo = geometry(H, y[1], y[2], KAHAN ? -c[1] : 0.0f, KAHAN ? -c[2] : 0.0f);
                         }
                     }
                 }
@@ -510,7 +563,7 @@ template <int MODE> __global__ void __launch_bounds__(128) trace32_kernel(TraceA
                 if (handoff_now)
                     v.L[hb + rank] = (int)id;
             }
-            if ((int64_t)base + cnt >= A.n)
+            if ((int64_t)base + cnt >= nq)
                 exhausted = true;
         }
         if (!__any_sync(FULL, has))
@@ -532,7 +585,7 @@ template <int MODE> __global__ void __launch_bounds__(128) trace32_kernel(TraceA
                     handoff = true;
                 } else {
                     const int e0 = euler;
-                    status = step_once<float, KAHAN>(H, O, y, c, fin, euler, remaps);
+                    status = step_once<float, KAHAN>(H, O, y, c, geo, fin, euler, remaps);
                     tot_euler += (unsigned long long)(euler - e0);
                     ++steps;
                     ++used;
@@ -563,10 +616,8 @@ template <int MODE> __global__ void __launch_bounds__(128) trace32_kernel(TraceA
     warp_stats<float>(A, lane, tot_steps, tot_euler, 0ull);
 }
 
-// Double-precision persistent tracer.  LIST = false: every ray of a GRAY_FP64
-// buffer.  LIST = true: the rays of the hand-off list of a
-// GRAY_FP32_KAHAN_SEL64 buffer (states in its single-precision planes).
-template <bool LIST> __global__ void __launch_bounds__(128) trace64_kernel(TraceArgs A)
+// Double-precision persistent tracer over every ray of a GRAY_FP64 buffer.
+__global__ void __launch_bounds__(128) trace64_kernel(TraceArgs A)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -576,12 +627,123 @@ template <bool LIST> __global__ void __launch_bounds__(128) trace64_kernel(Trace
     O.h_min = A.h_min;
     O.eps_xi = A.eps_xi;
     O.step_rule = A.step_rule;
-    const int64_t n = LIST ? (int64_t)*(volatile unsigned long long *)&A.ws->handoff : A.n;
 
     bool has = false, exhausted = false;
     int64_t id = 0;
     double y[8], cz[8], fin[4];
     Hole<double> H;
+    Geo<double> geo;
+    int steps = 0, euler = 0, remaps = 0, n64 = 0, used = 0;
+    unsigned long long tot_steps = 0, tot_euler = 0;
+    const int64_t nq = queue_length(A);
+#pragma unroll
+    for (int m = 0; m < 8; ++m)
+        cz[m] = 0.0;
+
+    for (;;) {
+        while (!exhausted) {
+            const unsigned idle = __ballot_sync(FULL, !has);
+            if (idle == 0)
+                break;
+            const int cnt = __popc(idle);
+            const int leader = __ffs(idle) - 1;
+            unsigned long long base = 0;
+            if (lane == leader)
+                base = atomicAdd(&A.ws->head, (unsigned long long)cnt);
+            base = __shfl_sync(FULL, base, leader);
+            if (!has) {
+                const int64_t slot = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
+                const int64_t my = slot < nq ? queue_ray(A, slot) : -1;
+                if (my >= 0) {
+                    const int4 s0 = v.S0[my];
+                    if (s0.x == GRAY_RAY_ACTIVE) {
+                        const int4 s1 = v.S1[my];
+                        has = true;
+                        id = my;
+                        steps = s0.y;
+                        euler = s0.z;
+                        remaps = s0.w;
+                        n64 = s1.x;
+                        used = (s1.y == A.epoch) ? s1.z : 0;
+                        const d4 p = ld_d4(v.P, my);
+                        H = make_hole(p.x, p.y, p.z, A.cap_frac, A.r_esc_frac, A.r_sw);
+                        const d4 X = ld_d4(v.X, my), K = ld_d4(v.K, my);
+                        y[0] = X.x; y[1] = X.y; y[2] = X.z; y[3] = X.w;
+                        y[4] = K.x; y[5] = K.y; y[6] = K.z; y[7] = K.w;
+                        geo = geometry(H, y[1], y[2]);
+                    }
+                }
+            }
+            if ((int64_t)base + cnt >= nq)
+                exhausted = true;
+        }
+        if (!__any_sync(FULL, has))
+            break;
+
+        for (int k = 0; k < A.refill; ++k) {
+            if (has) {
+                int status = GRAY_RAY_ACTIVE;
+                bool yield = false;
+                if (steps >= A.max_steps) {
+                    status = GRAY_RAY_STEP_CAP;
+                    for (int m = 0; m < 4; ++m)
+                        fin[m] = y[m];
+                } else if (A.budget > 0 && used >= A.budget) {
+                    yield = true;
+                } else {
+                    const int e0 = euler;
+                    status = step_once<double, false>(H, O, y, cz, geo, fin, euler, remaps);
+                    tot_euler += (unsigned long long)(euler - e0);
+                    ++steps;
+                    ++used;
+                    ++tot_steps;
+                }
+                if (status != GRAY_RAY_ACTIVE || yield) {
+                    st_d4(v.X, id, y[0], y[1], y[2], y[3]);
+                    st_d4(v.K, id, y[4], y[5], y[6], y[7]);
+                    if (status != GRAY_RAY_ACTIVE)
+                        st_d4(v.F, id, fin[0], fin[1], fin[2], fin[3]);
+                    v.S0[id] = make_int4(status, steps, euler, remaps);
+                    v.S1[id] = make_int4(n64, A.epoch, used, 0);
+                    has = false;
+                }
+            }
+        }
+    }
+    warp_stats<double>(A, lane, tot_steps, tot_euler, 0ull);
+}
+
+// Zone kernel of GRAY_FP32_KAHAN_SEL64: the rays of the hand-off list, in
+// double precision while r < r_demote (= r_promote + r_sw) and in compensated
+// single precision once they climb out, switching back when they fall below
+// r_promote again -- so every handed-off ray finishes here and no further
+// single-precision pass is needed.  The switches are exact one way (hi - lo
+// to double) and a rounding the other way (double to hi, lo).
+__global__ void __launch_bounds__(128, 1) zone_kernel(TraceArgs A)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const StateView &v = A.v;
+    StepOpt<double> Od;
+    Od.h_frac = A.h_frac;
+    Od.h_min = A.h_min;
+    Od.eps_xi = A.eps_xi;
+    Od.step_rule = A.step_rule;
+    StepOpt<float> Of;
+    Of.h_frac = (float)A.h_frac;
+    Of.h_min = (float)A.h_min;
+    Of.eps_xi = (float)A.eps_xi;
+    Of.step_rule = A.step_rule;
+    const int64_t n = (int64_t)*(volatile unsigned long long *)&A.ws->handoff;
+
+    bool has = false, exhausted = false, dbl = true;
+    int64_t id = 0;
+    double yd[8], cz[8], find[4];
+    float yf[8], cf[8], finf[4];
+    Hole<double> Hd;
+    Hole<float> Hf;
+    Geo<double> gd;
+    Geo<float> gf;
     double r_demote = INFINITY;
     int steps = 0, euler = 0, remaps = 0, n64 = 0, used = 0;
     unsigned long long tot_steps = 0, tot_euler = 0, tot_fp64 = 0;
@@ -603,11 +765,12 @@ template <bool LIST> __global__ void __launch_bounds__(128) trace64_kernel(Trace
             if (!has) {
                 const int64_t slot = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
                 if (slot < n) {
-                    const int64_t my = LIST ? (int64_t)v.L[slot] : slot;
+                    const int64_t my = (int64_t)v.L[slot];
                     const int4 s0 = v.S0[my];
                     if (s0.x == GRAY_RAY_ACTIVE) {
                         const int4 s1 = v.S1[my];
                         has = true;
+                        dbl = true;
                         id = my;
                         steps = s0.y;
                         euler = s0.z;
@@ -615,26 +778,25 @@ template <bool LIST> __global__ void __launch_bounds__(128) trace64_kernel(Trace
                         n64 = s1.x;
                         used = (s1.y == A.epoch) ? s1.z : 0;
                         const d4 p = ld_d4(v.P, my);
-                        H = make_hole(p.x, p.y, p.z, A.cap_frac, A.r_esc_frac, A.r_sw);
-                        r_demote = H.r_promote + A.r_sw;
-                        if (!LIST) {
-                            const d4 X = ld_d4(v.X, my), K = ld_d4(v.K, my);
-                            y[0] = X.x; y[1] = X.y; y[2] = X.z; y[3] = X.w;
-                            y[4] = K.x; y[5] = K.y; y[6] = K.z; y[7] = K.w;
-                        } else if (s1.w & FLAG_DOUBLE_REPR) {
+                        Hd = make_hole(p.x, p.y, p.z, A.cap_frac, A.r_esc_frac, A.r_sw);
+                        Hf = make_hole_f(v.PF0[my], v.PF1[my], (float)A.cap_frac, (float)A.r_esc_frac,
+                                         (float)A.r_sw);
+                        r_demote = Hd.r_promote + A.r_sw;
+                        if (s1.w & FLAG_DOUBLE_REPR) {
                             // exact double state parked in the four single planes
                             const double2 q0 = ((const double2 *)v.X)[my], q1 = ((const double2 *)v.K)[my];
                             const double2 q2 = ((const double2 *)v.CX)[my], q3 = ((const double2 *)v.CK)[my];
-                            y[0] = q0.x; y[1] = q0.y; y[2] = q1.x; y[3] = q1.y;
-                            y[4] = q2.x; y[5] = q2.y; y[6] = q3.x; y[7] = q3.y;
+                            yd[0] = q0.x; yd[1] = q0.y; yd[2] = q1.x; yd[3] = q1.y;
+                            yd[4] = q2.x; yd[5] = q2.y; yd[6] = q3.x; yd[7] = q3.y;
                         } else {
                             const float4 X = ld_f4(v.X, my), K = ld_f4(v.K, my);
                             const float4 CX = ld_f4(v.CX, my), CK = ld_f4(v.CK, my);
-                            y[0] = (double)X.x - CX.x; y[1] = (double)X.y - CX.y;
-                            y[2] = (double)X.z - CX.z; y[3] = (double)X.w - CX.w;
-                            y[4] = (double)K.x - CK.x; y[5] = (double)K.y - CK.y;
-                            y[6] = (double)K.z - CK.z; y[7] = (double)K.w - CK.w;
+                            yd[0] = (double)X.x - CX.x; yd[1] = (double)X.y - CX.y;
+                            yd[2] = (double)X.z - CX.z; yd[3] = (double)X.w - CX.w;
+                            yd[4] = (double)K.x - CK.x; yd[5] = (double)K.y - CK.y;
+                            yd[6] = (double)K.z - CK.z; yd[7] = (double)K.w - CK.w;
                         }
+                        gd = geometry(Hd, yd[1], yd[2]);
                     }
                 }
             }
@@ -645,68 +807,76 @@ template <bool LIST> __global__ void __launch_bounds__(128) trace64_kernel(Trace
             break;
 
         for (int k = 0; k < A.refill; ++k) {
-            bool demote = false;
-            if (has) {
-                int status = GRAY_RAY_ACTIVE;
-                bool yield = false;
-                if (steps >= A.max_steps) {
-                    status = GRAY_RAY_STEP_CAP;
-                    for (int m = 0; m < 4; ++m)
-                        fin[m] = y[m];
-                } else if (A.budget > 0 && used >= A.budget) {
-                    yield = true;
-                } else if (LIST && y[1] >= r_demote) {
-                    demote = true;
-                } else {
-                    const int e0 = euler;
-                    status = step_once<double, false>(H, O, y, cz, fin, euler, remaps);
-                    tot_euler += (unsigned long long)(euler - e0);
-                    ++steps;
-                    ++used;
-                    ++tot_steps;
-                    if (LIST) {
-                        ++n64;
-                        ++tot_fp64;
-                    }
-                }
-                if (status != GRAY_RAY_ACTIVE || yield || demote) {
-                    int flags = 0;
-                    if (!LIST) {
-                        st_d4(v.X, id, y[0], y[1], y[2], y[3]);
-                        st_d4(v.K, id, y[4], y[5], y[6], y[7]);
-                        if (status != GRAY_RAY_ACTIVE)
-                            st_d4(v.F, id, fin[0], fin[1], fin[2], fin[3]);
-                    } else if (yield) {
-                        // park the exact double state; the ray resumes in double
-                        ((double2 *)v.X)[id] = make_double2(y[0], y[1]);
-                        ((double2 *)v.K)[id] = make_double2(y[2], y[3]);
-                        ((double2 *)v.CX)[id] = make_double2(y[4], y[5]);
-                        ((double2 *)v.CK)[id] = make_double2(y[6], y[7]);
-                        flags = FLAG_DOUBLE_MODE | FLAG_DOUBLE_REPR;
-                    } else {
-                        // back to a compensated single-precision pair (hi, hi - y)
-                        float hi[8], lo[8];
+            if (!has)
+                continue;
+            int status = GRAY_RAY_ACTIVE;
+            bool yield = false;
+            if (steps >= A.max_steps) {
+                status = GRAY_RAY_STEP_CAP;
+                for (int m = 0; m < 4; ++m)
+                    find[m] = dbl ? yd[m] : (double)yf[m] - (double)cf[m];
+            } else if (A.budget > 0 && used >= A.budget) {
+                yield = true;
+            } else if (dbl && yd[1] >= r_demote) {
+                // climb out of the zone: back to a compensated single pair
 #pragma unroll
-                        for (int m = 0; m < 8; ++m) {
-                            hi[m] = (float)y[m];
-                            lo[m] = (float)((double)hi[m] - y[m]);
-                        }
-                        st_f4(v.X, id, hi[0], hi[1], hi[2], hi[3]);
-                        st_f4(v.K, id, hi[4], hi[5], hi[6], hi[7]);
-                        st_f4(v.CX, id, lo[0], lo[1], lo[2], lo[3]);
-                        st_f4(v.CK, id, lo[4], lo[5], lo[6], lo[7]);
-                        if (status != GRAY_RAY_ACTIVE)
-                            st_f4(v.F, id, (float)fin[0], (float)fin[1], (float)fin[2], (float)fin[3]);
-                    }
-                    v.S0[id] = make_int4(status, steps, euler, remaps);
-                    v.S1[id] = make_int4(n64, A.epoch, used, flags);
-                    has = false;
+                for (int m = 0; m < 8; ++m) {
+                    yf[m] = (float)yd[m];
+                    cf[m] = (float)((double)yf[m] - yd[m]);
                 }
+                gf = geometry(Hf, yf[1], yf[2], -cf[1], -cf[2]);
+                dbl = false;
+                continue;
+            } else if (!dbl && yf[1] - cf[1] < Hf.r_promote) {
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    yd[m] = (double)yf[m] - (double)cf[m];
+                gd = geometry(Hd, yd[1], yd[2]);
+                dbl = true;
+                continue;
+            } else {
+                const int e0 = euler;
+                if (dbl) {
+                    status = step_once<double, false>(Hd, Od, yd, cz, gd, find, euler, remaps);
+                    ++n64;
+                    ++tot_fp64;
+                } else {
+                    status = step_once<float, true>(Hf, Of, yf, cf, gf, finf, euler, remaps);
+                    for (int m = 0; m < 4; ++m)
+                        find[m] = finf[m];
+                }
+                tot_euler += (unsigned long long)(euler - e0);
+                ++steps;
+                ++used;
+                ++tot_steps;
             }
-            if (LIST) {
-                int rank;
-                (void)warp_count(&A.ws->demoted, demote, lane, &rank);
+            if (status == GRAY_RAY_ACTIVE && !yield)
+                continue;
+            int flags = 0;
+            if (yield && dbl) {
+                // park the exact double state; the ray resumes in double
+                ((double2 *)v.X)[id] = make_double2(yd[0], yd[1]);
+                ((double2 *)v.K)[id] = make_double2(yd[2], yd[3]);
+                ((double2 *)v.CX)[id] = make_double2(yd[4], yd[5]);
+                ((double2 *)v.CK)[id] = make_double2(yd[6], yd[7]);
+                flags = FLAG_DOUBLE_MODE | FLAG_DOUBLE_REPR;
+            } else {
+                float hi[8], lo[8];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) {
+                    hi[m] = dbl ? (float)yd[m] : yf[m];
+                    lo[m] = dbl ? (float)((double)hi[m] - yd[m]) : cf[m];
+                }
+                st_f4(v.X, id, hi[0], hi[1], hi[2], hi[3]);
+                st_f4(v.K, id, hi[4], hi[5], hi[6], hi[7]);
+                st_f4(v.CX, id, lo[0], lo[1], lo[2], lo[3]);
+                st_f4(v.CK, id, lo[4], lo[5], lo[6], lo[7]);
+                if (status != GRAY_RAY_ACTIVE)
+                    st_f4(v.F, id, (float)find[0], (float)find[1], (float)find[2], (float)find[3]);
             }
+            v.S0[id] = make_int4(status, steps, euler, remaps);
+            v.S1[id] = make_int4(n64, A.epoch, used, flags);
+            has = false;
         }
     }
     warp_stats<double>(A, lane, tot_steps, tot_euler, tot_fp64);
@@ -723,6 +893,124 @@ __global__ void count_active_kernel(const int4 *S0, int64_t n, unsigned long lon
         mine += __shfl_xor_sync(0xffffffffu, mine, off);
     if ((threadIdx.x & 31) == 0 && mine)
         atomicAdd(out, mine);
+}
+
+// --------------------------------------------------------------------------
+// Planning: longest-first order of the rays of a set of images
+// --------------------------------------------------------------------------
+//
+// A ray's cost (its number of steps) varies by an order of magnitude across
+// an image (rays grazing a pole or the photon orbit take longest), and a
+// persistent queue finishes only when its last long ray does; a long ray
+// taken from the queue late therefore sets the length of the whole launch.
+// gray_plan traces a sparse probe grid first (every stride-th pixel in both
+// directions, with a small step budget), predicts each pixel's cost from the
+// probes of its cell, and writes a queue of the image rays in descending
+// predicted cost (a counting sort over PLAN_BUCKETS buckets).  The probe rays
+// keep the progress they made.  A ray's result does not depend on its place
+// in the queue.
+
+constexpr int PLAN_BUCKETS = 64;
+// aux layout: [0] probe count, [1..64] histogram, [65..128] bucket offsets
+constexpr int AUX_PROBES = 0, AUX_HIST = 1, AUX_OFF = 1 + PLAN_BUCKETS, AUX_WORDS = 1 + 2 * PLAN_BUCKETS;
+
+__device__ __forceinline__ int image_of(const ImageDev *imgs, int n_images, int64_t i)
+{
+    int lo = 0, hi = n_images - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (imgs[mid].first <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void probe_list_kernel(const ImageDev *imgs, int n_images, int64_t total, int64_t first_ray, int stride,
+                                  int *list, unsigned long long *aux)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool probe = false;
+    if (i < total) {
+        const ImageDev im = imgs[image_of(imgs, n_images, i)];
+        const int64_t p = i - im.first, row = p / im.nx, col = p - row * im.nx;
+        probe = (row % stride == 0) && (col % stride == 0);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, probe);
+    if (!m)
+        return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader)
+        base = atomicAdd(&aux[AUX_PROBES], (unsigned long long)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (probe)
+        list[base + __popc(m & ((1u << lane) - 1u))] = (int)(first_ray + i);
+}
+
+// Predicted cost of pixel i: the largest probe cost among the 4 x 4 probes
+// around its probe cell (the cell's corners and one ring beyond, so that thin
+// long-ray features between probes are not missed); a probe that finished
+// costs its steps, one that did not costs its steps plus eight per Euler redo
+// (a ray crawling past a pole on redos is a long one).
+__device__ __forceinline__ int plan_bucket(const ImageDev *imgs, int n_images, int64_t i, int64_t first_ray,
+                                           int stride, int budget, const int4 *S0)
+{
+    const ImageDev im = imgs[image_of(imgs, n_images, i)];
+    const int64_t p = i - im.first, row = p / im.nx, col = p - row * im.nx;
+    const int64_t r0 = row - row % stride, c0 = col - col % stride;
+    float cost = 0.0f;
+    for (int dr = -1; dr < 3; ++dr)
+        for (int dc = -1; dc < 3; ++dc) {
+            const int64_t rr = r0 + dr * stride, cc = c0 + dc * stride;
+            if (rr < 0 || cc < 0 || rr >= im.ny || cc >= im.nx)
+                continue;
+            const int4 q = S0[first_ray + im.first + rr * im.nx + cc];
+            const float c = (q.x == GRAY_RAY_ACTIVE) ? (float)q.y + 8.0f * (float)q.z : (float)q.y;
+            cost = fmaxf(cost, c);
+        }
+    int b = (int)(cost * (float)(PLAN_BUCKETS / 2) / (float)budget);
+    return b < 0 ? 0 : (b >= PLAN_BUCKETS ? PLAN_BUCKETS - 1 : b);
+}
+
+__global__ void plan_hist_kernel(const ImageDev *imgs, int n_images, int64_t total, int64_t first_ray, int stride,
+                                 int budget, const int4 *S0, unsigned long long *aux)
+{
+    __shared__ unsigned int h[PLAN_BUCKETS];
+    for (int k = threadIdx.x; k < PLAN_BUCKETS; k += blockDim.x)
+        h[k] = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < total)
+        atomicAdd(&h[plan_bucket(imgs, n_images, i, first_ray, stride, budget, S0)], 1u);
+    __syncthreads();
+    for (int k = threadIdx.x; k < PLAN_BUCKETS; k += blockDim.x)
+        if (h[k])
+            atomicAdd(&aux[AUX_HIST + k], (unsigned long long)h[k]);
+}
+
+// Offsets for descending buckets (one warp; PLAN_BUCKETS <= 64).
+__global__ void plan_scan_kernel(unsigned long long *aux)
+{
+    if (threadIdx.x != 0)
+        return;
+    unsigned long long run = 0;
+    for (int b = PLAN_BUCKETS - 1; b >= 0; --b) {
+        aux[AUX_OFF + b] = run;
+        run += aux[AUX_HIST + b];
+    }
+}
+
+__global__ void plan_scatter_kernel(const ImageDev *imgs, int n_images, int64_t total, int64_t first_ray, int stride,
+                                    int budget, const int4 *S0, unsigned long long *aux, int *order)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total)
+        return;
+    const int b = plan_bucket(imgs, n_images, i, first_ray, stride, budget, S0);
+    const unsigned long long pos = atomicAdd(&aux[AUX_OFF + b], 1ull);
+    order[pos] = (int)(first_ray + i);
 }
 
 // --------------------------------------------------------------------------
@@ -963,7 +1251,8 @@ int validate_image(const gray_image &im)
 
 int check_state(const gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_state)
 {
-    if (!ctx || !state || n_state < 0)
+    // ray indices are 32-bit in the queues (2^31 rays would need ~390 GB)
+    if (!ctx || !state || n_state < 0 || n_state > 0x7fffffff)
         return GRAY_EINVAL;
     if (state_bytes < gray_state_bytes(n_state, ctx->opt.precision))
         return GRAY_EINVAL;
@@ -1067,6 +1356,12 @@ int gray_create(gray_ctx **ctx, const gray_options *opt)
         delete c;
         return GRAY_ENOMEM;
     }
+    if (cudaMalloc((void **)&c->aux, AUX_WORDS * sizeof(unsigned long long)) != cudaSuccess) {
+        cudaFree(c->ws);
+        cudaFreeHost(c->ws_host);
+        delete c;
+        return GRAY_ENOMEM;
+    }
     std::memset(c->ws_host, 0, sizeof(Workspace));
     *ctx = c;
     return GRAY_OK;
@@ -1077,6 +1372,7 @@ void gray_destroy(gray_ctx *ctx)
     if (!ctx)
         return;
     cudaFree(ctx->ws);
+    cudaFree(ctx->aux);
     cudaFreeHost(ctx->ws_host);
     delete ctx;
 }
@@ -1128,24 +1424,24 @@ int gray_setup_rays(gray_ctx *ctx, const double *rays, int64_t n, double M, void
     return check_launch();
 }
 
-int gray_trace(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, int64_t step_budget,
-               int64_t *n_active_host, int64_t *stats_host, void *stream)
+} // extern "C"
+
+namespace {
+
+TraceArgs make_trace_args(gray_ctx *ctx, void *state, int64_t n_state, int64_t step_budget)
 {
-    int rc = check_state(ctx, state, state_bytes, n_state);
-    if (rc)
-        return rc;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemsetAsync(ctx->ws, 0, sizeof(Workspace), s) != cudaSuccess)
-        return GRAY_ECUDA;
     const gray_options &o = ctx->opt;
-    ctx->epoch = ctx->epoch == 0x7fffffff ? 1 : ctx->epoch + 1;
     TraceArgs A;
     A.v = make_view(state, n_state, o.precision);
     A.n = n_state;
+    A.order = nullptr;
+    A.n_queue = n_state;
+    A.n_queue_dev = nullptr;
     A.budget = step_budget;
     A.max_steps = o.max_steps;
-    A.refill = o.refill > 0 ? o.refill : 8;
+    A.refill = o.refill > 0 ? o.refill : 16;
     A.step_rule = o.step_rule;
+    ctx->epoch = ctx->epoch == 0x7fffffff ? 1 : ctx->epoch + 1;
     A.epoch = ctx->epoch;
     A.h_frac = o.h_frac;
     A.h_min = o.h_min;
@@ -1154,67 +1450,83 @@ int gray_trace(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, 
     A.r_esc_frac = o.r_esc_frac;
     A.r_sw = o.r_sw;
     A.ws = ctx->ws;
-    const int block = o.block > 0 ? o.block : 128;
-    // persistent grid: resident blocks per SM x SMs, never more blocks than work
-    auto grid_of = [&](const void *kernel, int64_t work) -> unsigned {
-        int per_sm = o.blocks_per_sm;
-        if (per_sm <= 0) {
+    return A;
+}
+
+// Persistent grid: resident blocks per SM x SMs, never more blocks than work.
+unsigned persistent_grid(const gray_ctx *ctx, const void *kernel, int block, int64_t work)
+{
+    int per_sm = ctx->opt.blocks_per_sm;
+    if (per_sm <= 0) {
+        per_sm = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1)
             per_sm = 1;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1)
-                per_sm = 1;
-        }
-        int64_t want = (int64_t)per_sm * ctx->num_sms;
-        const int64_t need = (work + block - 1) / block;
-        if (want > need)
-            want = need;
-        return (unsigned)(want > 0 ? want : 1);
-    };
-    const bool sel64 = o.precision == GRAY_FP32_KAHAN_SEL64;
-    if (n_state > 0) {
-        switch (o.precision) {
-        case GRAY_FP64:
-            trace64_kernel<false><<<grid_of((const void *)trace64_kernel<false>, n_state), block, 0, s>>>(A);
-            break;
-        case GRAY_FP32:
-            trace32_kernel<GRAY_FP32><<<grid_of((const void *)trace32_kernel<GRAY_FP32>, n_state), block, 0, s>>>(A);
-            break;
-        case GRAY_FP32_KAHAN:
-            trace32_kernel<GRAY_FP32_KAHAN>
-                <<<grid_of((const void *)trace32_kernel<GRAY_FP32_KAHAN>, n_state), block, 0, s>>>(A);
-            break;
-        default:
-            break;
-        }
-        if (!sel64 && (rc = check_launch()))
+    }
+    int64_t want = (int64_t)per_sm * ctx->num_sms;
+    const int64_t need = (work + block - 1) / block;
+    if (want > need)
+        want = need;
+    return (unsigned)(want > 0 ? want : 1);
+}
+
+// One single- or double-precision pass over the queue of A (no zone kernel).
+int launch_pass(gray_ctx *ctx, const TraceArgs &A, int64_t work, cudaStream_t s)
+{
+    const int block = ctx->opt.block > 0 ? ctx->opt.block : 128;
+    switch (ctx->opt.precision) {
+    case GRAY_FP64:
+        trace64_kernel<<<persistent_grid(ctx, (const void *)trace64_kernel, block, work), block, 0, s>>>(A);
+        break;
+    case GRAY_FP32:
+        trace32_kernel<GRAY_FP32>
+            <<<persistent_grid(ctx, (const void *)trace32_kernel<GRAY_FP32>, block, work), block, 0, s>>>(A);
+        break;
+    case GRAY_FP32_KAHAN:
+        trace32_kernel<GRAY_FP32_KAHAN>
+            <<<persistent_grid(ctx, (const void *)trace32_kernel<GRAY_FP32_KAHAN>, block, work), block, 0, s>>>(A);
+        break;
+    default:
+        trace32_kernel<GRAY_FP32_KAHAN_SEL64>
+            <<<persistent_grid(ctx, (const void *)trace32_kernel<GRAY_FP32_KAHAN_SEL64>, block, work), block, 0, s>>>(
+                A);
+        break;
+    }
+    return check_launch();
+}
+
+} // namespace
+
+extern "C" {
+
+int gray_trace(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, const int32_t *order, int64_t n_order,
+               int64_t step_budget, int64_t *n_active_host, int64_t *stats_host, void *stream)
+{
+    int rc = check_state(ctx, state, state_bytes, n_state);
+    if (rc)
+        return rc;
+    if (order ? n_order < 0 : n_order != 0)
+        return GRAY_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemsetAsync(ctx->ws, 0, sizeof(Workspace), s) != cudaSuccess)
+        return GRAY_ECUDA;
+    TraceArgs A = make_trace_args(ctx, state, n_state, step_budget);
+    if (order) {
+        A.order = order;
+        A.n_queue = n_order;
+    }
+    const int64_t work = order ? n_order : n_state;
+    if (n_state > 0 && work > 0) {
+        if ((rc = launch_pass(ctx, A, work, s)))
             return rc;
-        // Selective double: alternate a single-precision pass over the buffer
-        // and a double-precision pass over the hand-off list until no ray is
-        // handed off or returned; the host reads two counters between passes.
-        const unsigned g32 = grid_of((const void *)trace32_kernel<GRAY_FP32_KAHAN_SEL64>, n_state);
-        for (int round = 0; sel64 && round < 1000; ++round) {
-            trace32_kernel<GRAY_FP32_KAHAN_SEL64><<<g32, block, 0, s>>>(A);
-            if ((rc = check_launch()))
-                return rc;
-            if (cudaMemcpyAsync(ctx->ws_host, ctx->ws, sizeof(Workspace), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess)
-                return GRAY_ECUDA;
-            const unsigned long long handed = ctx->ws_host->handoff;
-            if (handed == 0)
-                break;
+        if (ctx->opt.precision == GRAY_FP32_KAHAN_SEL64) {
+            // the zone kernel takes the rays the single pass handed off (the
+            // count stays on the device)
             if (cudaMemsetAsync(&ctx->ws->head, 0, sizeof(unsigned long long), s) != cudaSuccess)
                 return GRAY_ECUDA;
-            trace64_kernel<true><<<grid_of((const void *)trace64_kernel<true>, (int64_t)handed), block, 0, s>>>(A);
+            const int block = ctx->opt.block > 0 ? ctx->opt.block : 128;
+            zone_kernel<<<persistent_grid(ctx, (const void *)zone_kernel, block, work), block, 0, s>>>(A);
             if ((rc = check_launch()))
                 return rc;
-            if (cudaMemcpyAsync(ctx->ws_host, ctx->ws, sizeof(Workspace), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                cudaStreamSynchronize(s) != cudaSuccess)
-                return GRAY_ECUDA;
-            if (ctx->ws_host->demoted == 0)
-                break;
-            // next round: fresh queue, empty hand-off list
-            if (cudaMemsetAsync(&ctx->ws->head, 0, sizeof(unsigned long long), s) != cudaSuccess ||
-                cudaMemsetAsync(&ctx->ws->handoff, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess)
-                return GRAY_ECUDA;
         }
     }
     if (!n_active_host && !stats_host)
@@ -1238,6 +1550,64 @@ int gray_trace(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, 
         stats_host[3] = (int64_t)w.active;
     }
     return w.active ? 1 : 0;
+}
+
+int gray_plan(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, const gray_image *images,
+              int32_t n_images, int64_t first_ray, int32_t probe_stride, int32_t probe_budget, int32_t *order,
+              size_t order_bytes, void *stream)
+{
+    int rc = check_state(ctx, state, state_bytes, n_state);
+    if (rc)
+        return rc;
+    if (!images || n_images < 1 || first_ray < 0 || !order || probe_stride < 1 || probe_stride > 65536 ||
+        probe_budget < 1)
+        return GRAY_EINVAL;
+    for (int k = 0; k < n_images; ++k)
+        if ((rc = validate_image(images[k])))
+            return rc;
+    int64_t total = 0;
+    std::vector<ImageDev> t = image_table(images, n_images, total);
+    if (first_ray + total > n_state || order_bytes < sizeof(int32_t) * (size_t)total)
+        return GRAY_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *dimg = nullptr;
+    if ((rc = upload_table(t.data(), t.size() * sizeof(ImageDev), s, &dimg)))
+        return rc;
+    const ImageDev *im = (const ImageDev *)dimg;
+    if (cudaMemsetAsync(ctx->aux, 0, AUX_WORDS * sizeof(unsigned long long), s) != cudaSuccess ||
+        cudaMemsetAsync(ctx->ws, 0, sizeof(Workspace), s) != cudaSuccess)
+        return GRAY_ECUDA;
+    // 1. the probe list (written into the order buffer), 2. the probes traced
+    // under the probe budget
+    probe_list_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, probe_stride, order,
+                                                          ctx->aux);
+    if ((rc = check_launch()))
+        return rc;
+    TraceArgs A = make_trace_args(ctx, state, n_state, probe_budget);
+    A.order = order;
+    A.n_queue_dev = &ctx->aux[AUX_PROBES];
+    int64_t probes_max = 0;
+    for (int k = 0; k < n_images; ++k)
+        probes_max += (int64_t)((images[k].nx + probe_stride - 1) / probe_stride) *
+                      ((images[k].ny + probe_stride - 1) / probe_stride);
+    if ((rc = launch_pass(ctx, A, probes_max, s)))
+        return rc;
+    // 3. predicted cost -> bucket histogram -> descending offsets -> queue
+    const StateView v = make_view(state, n_state, ctx->opt.precision);
+    plan_hist_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, probe_stride, probe_budget,
+                                                         v.S0, ctx->aux);
+    if ((rc = check_launch()))
+        return rc;
+    plan_scan_kernel<<<1, 32, 0, s>>>(ctx->aux);
+    if ((rc = check_launch()))
+        return rc;
+    plan_scatter_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, probe_stride,
+                                                            probe_budget, v.S0, ctx->aux, order);
+    rc = check_launch();
+    cudaError_t e = cudaFreeAsync(dimg, s);
+    if (rc)
+        return rc;
+    return cuda_err(e);
 }
 
 int gray_render(gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_state, int64_t first_ray, int64_t n,

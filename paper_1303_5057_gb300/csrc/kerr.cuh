@@ -52,6 +52,7 @@ template <> __device__ __forceinline__ double pi_v<double>() { return 3.14159265
 template <typename T> struct Hole {
     T a, M;
     T rp, rm, dc; // Delta = (r - rp)(r - rm) + dc
+    T rp_lo;      // single precision: rp - (float)rp, so rp is carried to ~48 bits
     T r_h;        // horizon used by the step guard; -inf when M = 0 (no guard)
     T r_cap;      // capture radius cap_frac * r_h; -1 when M = 0 (no capture)
     T r_esc;      // escape radius
@@ -76,6 +77,7 @@ __host__ __device__ inline Hole<double> make_hole(double a, double M, double r_o
     H.rp = M + root;
     H.rm = M - root;
     H.dc = disc < 0.0 ? -disc : 0.0;
+    H.rp_lo = 0.0;
     if (M > 0.0) {
         H.r_h = H.rp;
         H.r_cap = cap_frac * H.rp;
@@ -95,6 +97,7 @@ template <typename T> __host__ __device__ inline Hole<T> cast_hole(const Hole<do
     o.a = (T)h.a;
     o.M = (T)h.M;
     o.rp = (T)h.rp;
+    o.rp_lo = (T)(h.rp - (double)o.rp);
     o.rm = (T)h.rm;
     o.dc = (T)h.dc;
     o.r_h = (T)h.r_h;
@@ -102,6 +105,43 @@ template <typename T> __host__ __device__ inline Hole<T> cast_hole(const Hole<do
     o.r_esc = (T)h.r_esc;
     o.r_promote = (T)h.r_promote;
     return o;
+}
+
+// Single-precision per-ray constants, computed once in double at set-up and
+// stored as two float4: (a, M, r_+ high, r_+ low) and (r_-, dc, r_h, r_obs).
+__host__ __device__ inline void hole_constants_f(double a, double M, double r_obs, float *c8)
+{
+    const Hole<double> H = make_hole(a, M, r_obs, 1.0, 1.0, 0.0);
+    const float rp_hi = (float)H.rp;
+    c8[0] = (float)a;
+    c8[1] = (float)M;
+    c8[2] = rp_hi;
+    c8[3] = (float)(H.rp - (double)rp_hi);
+    c8[4] = (float)H.rm;
+    c8[5] = (float)H.dc;
+    c8[6] = (float)H.r_h;
+    c8[7] = (float)r_obs;
+}
+
+__device__ __forceinline__ Hole<float> make_hole_f(float4 c0, float4 c1, float cap_frac, float r_esc_frac, float r_sw)
+{
+    Hole<float> H;
+    H.a = c0.x;
+    H.M = c0.y;
+    H.rp = c0.z;
+    H.rp_lo = c0.w;
+    H.rm = c1.x;
+    H.dc = c1.y;
+    H.r_h = c1.z;
+    if (H.M > 0.0f) {
+        H.r_cap = cap_frac * H.r_h;
+        H.r_promote = H.r_cap + r_sw;
+    } else {
+        H.r_cap = -1.0f;
+        H.r_promote = -INFINITY;
+    }
+    H.r_esc = r_esc_frac * c1.w;
+    return H;
 }
 
 // Metric pieces at (r, theta) with sin/cos given.
@@ -183,42 +223,109 @@ __device__ inline void christoffel_closed_form(const Hole<T> &H, T r, T th, T *G
 #undef GSET
 }
 
+// Reciprocal.  Single precision: the hardware approximation refined by one
+// Newton-Raphson step r <- r (2 - x r) (about 1 ulp); double: a true divide.
+__device__ __forceinline__ float recip(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    const float e = fmaf(-x, r, 1.0f);
+    return fmaf(r, e, r);
+}
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+// Geometry of one point (r, theta): the quantities every right-hand side and
+// the Eq. 4 monitor need.  Single precision takes the three reciprocals from
+// one reciprocal of Sigma Delta sin(theta).
+template <typename T> struct Geo {
+    T r, s, c, Sigma, Delta, iS, iD, is;
+};
+
+// dr and dth are the low words of a compensated single-precision point (the
+// true point is (r + dr, th + dth)): sin and cos get their first-order
+// correction and Delta is formed from the compensated r and the split r_+, so
+// near theta = pi and near the horizon single precision keeps the bits that
+// the high words alone lose.
+template <typename T>
+__device__ __forceinline__ Geo<T> geometry(const Hole<T> &H, T r, T th, T dr = T(0), T dth = T(0))
+{
+    Geo<T> g;
+    g.r = r;
+    T s0, c0;
+    fsincos(th, &s0, &c0);
+    if (sizeof(T) == 4) {
+        g.s = fma(dth, c0, s0);
+        g.c = fma(-dth, s0, c0);
+        g.Delta = fma((r - H.rp) + (dr - H.rp_lo), (r - H.rm) + dr, H.dc);
+    } else {
+        g.s = s0;
+        g.c = c0;
+        g.Delta = fma(r - H.rp, r - H.rm, H.dc);
+    }
+    g.Sigma = fma(H.a * H.a, g.c * g.c, r * r);
+    if (sizeof(T) == 4) {
+        const T Ds = g.Delta * g.s, SD = g.Sigma * g.Delta;
+        const T inv = recip(SD * g.s);
+        g.iS = inv * Ds;
+        g.iD = inv * (g.Sigma * g.s);
+        g.is = inv * SD;
+    } else {
+        g.iS = T(1) / g.Sigma;
+        g.iD = T(1) / g.Delta;
+        g.is = T(1) / g.s;
+    }
+    return g;
+}
+
+// dk^mu/dl at a point whose geometry is known (same grouping as below).
+template <typename T>
+__device__ __forceinline__ void accel_geo(const Hole<T> &H, const Geo<T> &g, T kt, T kr, T kh, T kp, T *acc)
+{
+    const T a = H.a, M = H.M, r = g.r, s = g.s, c = g.c;
+    const T a2 = a * a, r2 = r * r, s2 = s * s, c2 = c * c, sc = s * c;
+    const T iS = g.iS, iD = g.iD, Delta = g.Delta;
+    const T iS2 = iS * iS;
+    const T A = fma(-a2, c2, r2), P = r2 + a2;
+    const T w = fma(-a * s2, kp, kt);
+    const T cot = c * g.is;
+    const T Mr = M * r;
+    const T u_t = fma(iS * P * A, w, -T(2) * a * r2 * s2 * kp);
+    acc[0] = -T(2) * M * iS * (iD * kr * u_t - T(2) * a2 * r * sc * iS * kh * w);
+    const T ang = fma(s2 * kp, kp, kh * kh);
+    const T u_r = -M * Delta * A * iS2 * w * w + Delta * r * ang - (a2 * r * s2 - M * A) * iD * kr * kr
+                  + T(2) * a2 * sc * kr * kh;
+    acc[1] = iS * u_r;
+    const T u_h = T(2) * Mr * a2 * iS2 * w * w - T(4) * Mr * a * iS * w * kp + P * kp * kp - a2 * iD * kr * kr
+                  + a2 * kh * kh;
+    acc[2] = iS * (sc * u_h - T(2) * r * kr * kh);
+    const T u_p1 = r * kp * (T(1) - T(2) * Mr * iS) + M * a * A * iS2 * w;
+    const T u_p2 = kp - T(2) * Mr * a * iS2 * w;
+    acc[3] = -T(2) * (kr * iD * u_p1 + cot * kh * u_p2);
+}
+
+// Eq. 4 test without its division: |xi + 1| > eps  <=>
+// |num + g_tt (k^t)^2| > eps |g_tt (k^t)^2| (NaN fails, as in the oracle).
+template <typename T> __device__ __forceinline__ bool xi_fails(const Hole<T> &H, const Geo<T> &g, const T *y, T eps)
+{
+    const T r = g.r, s2 = g.s * g.s, a2 = H.a * H.a;
+    const T twoMr = T(2) * H.M * r;
+    const T gtt = -(T(1) - twoMr * g.iS);
+    const T gtp = -twoMr * H.a * s2 * g.iS;
+    const T grr = g.Sigma * g.iD;
+    const T gpp = (r * r + a2 + twoMr * a2 * s2 * g.iS) * s2;
+    const T kt = y[4], kr = y[5], kh = y[6], kp = y[7];
+    const T num = grr * kr * kr + gpp * kp * kp + g.Sigma * kh * kh + T(2) * gtp * kt * kp;
+    const T den = gtt * kt * kt;
+    return !(fabs(num + den) <= eps * fabs(den));
+}
+
 // dk^mu/dl = -Gamma^mu_ab k^a k^b, from the closed-form symbols grouped with
 // w = k^t - a s^2 k^ph.  Inputs: r, theta and k = (kt, kr, kh, kp).
 template <typename T>
 __device__ __forceinline__ void geodesic_accel(const Hole<T> &H, T r, T th, T kt, T kr, T kh, T kp, T *acc)
 {
-    T s, c;
-    fsincos(th, &s, &c);
-    const T a = H.a, M = H.M;
-    const T a2 = a * a, r2 = r * r, s2 = s * s, c2 = c * c, sc = s * c;
-    const T Sigma = fma(a2, c2, r2);
-    const T Delta = fma(r - H.rp, r - H.rm, H.dc);
-    const T iS = T(1) / Sigma, iD = T(1) / Delta;
-    const T iS2 = iS * iS;
-    const T A = fma(-a2, c2, r2), P = r2 + a2;
-    const T w = fma(-a * s2, kp, kt);
-    const T cot = c / s;
-    const T Mr = M * r;
-    // t: -2 M/Sigma [ kr/Delta (P A w/Sigma - 2 a r^2 s^2 kp) - 2 a^2 r s c kh w/Sigma ]
-    const T u_t = fma(iS * P * A, w, -T(2) * a * r2 * s2 * kp);
-    acc[0] = -T(2) * M * iS * (iD * kr * u_t - T(2) * a2 * r * sc * iS * kh * w);
-    // r: [-M Delta A w^2/Sigma^2 + Delta r (s^2 kp^2 + kh^2)
-    //     - (a^2 r s^2 - M A) kr^2/Delta + 2 a^2 s c kr kh] / Sigma
-    const T ang = fma(s2 * kp, kp, kh * kh);
-    const T u_r = -M * Delta * A * iS2 * w * w + Delta * r * ang - (a2 * r * s2 - M * A) * iD * kr * kr
-                  + T(2) * a2 * sc * kr * kh;
-    acc[1] = iS * u_r;
-    // theta: { s c [2 M a^2 r w^2/Sigma^2 - 4 M a r w kp/Sigma + P kp^2
-    //          - a^2 kr^2/Delta + a^2 kh^2] - 2 r kr kh } / Sigma
-    const T u_h = T(2) * Mr * a2 * iS2 * w * w - T(4) * Mr * a * iS * w * kp + P * kp * kp - a2 * iD * kr * kr
-                  + a2 * kh * kh;
-    acc[2] = iS * (sc * u_h - T(2) * r * kr * kh);
-    // phi: -2 [ kr/Delta (r kp (1 - 2 M r/Sigma) + M a A w/Sigma^2)
-    //          + cot kh (kp - 2 M a r w/Sigma^2) ]
-    const T u_p1 = r * kp * (T(1) - T(2) * Mr * iS) + M * a * A * iS2 * w;
-    const T u_p2 = kp - T(2) * Mr * a * iS2 * w;
-    acc[3] = -T(2) * (kr * iD * u_p1 + cot * kh * u_p2);
+    const Geo<T> g = geometry(H, r, th);
+    accel_geo(H, g, kt, kr, kh, kp, acc);
 }
 
 // Step size (negative: backward trace).  Benchmark rule
@@ -227,12 +334,20 @@ __device__ __forceinline__ void geodesic_accel(const Hole<T> &H, T r, T th, T kt
 template <typename T> __device__ __forceinline__ T step_size(const Hole<T> &H, const StepOpt<T> &O, const T *y)
 {
     const T r = y[1], kr = y[5];
-    const T guard = (r - H.r_h) / (T(2) * fabs(kr));
-    T h;
-    if (O.step_rule == 1)
-        h = fmin(O.h_frac / (fabs(kr / r) + fabs(y[6]) + fabs(y[7])), guard);
-    else
-        h = fmin(O.h_frac * r, guard);
+    T guard, h;
+    if (sizeof(T) == 4) {
+        guard = (r - H.r_h) * (T(0.5) * recip(fabs(kr)));
+        if (O.step_rule == 1)
+            h = fmin(O.h_frac * recip(fabs(kr) * recip(r) + fabs(y[6]) + fabs(y[7])), guard);
+        else
+            h = fmin(O.h_frac * r, guard);
+    } else {
+        guard = (r - H.r_h) / (T(2) * fabs(kr));
+        if (O.step_rule == 1)
+            h = fmin(O.h_frac / (fabs(kr / r) + fabs(y[6]) + fabs(y[7])), guard);
+        else
+            h = fmin(O.h_frac * r, guard);
+    }
     h = fmax(h, O.h_min);
     return -h;
 }
@@ -252,25 +367,56 @@ template <typename T> struct BisectIters;
 template <> struct BisectIters<float> { static constexpr int value = 30; };
 template <> struct BisectIters<double> { static constexpr int value = 60; };
 
-// Final (t, r, theta, phi) on the stop surface r = r_stop: bisection of the
-// Hermite r(s) over the last step, then Hermite for the other coordinates,
-// then the pole remap of Eq. 3 applied to the interpolated point.
-template <typename T>
-__device__ inline void stop_surface(const T *y0, const T *y1, T h, T r_stop, T *fin)
+// Crossing fraction of the stop surface within the last step.  Double:
+// bisection of the Hermite r(s) - r_stop (60 halvings, as the oracle).  Single:
+// Newton's method from the secant estimate, kept inside the bracket (a Newton
+// step that leaves it is replaced by a bisection step), 6 iterations.
+template <typename T> __device__ __forceinline__ T crossing_fraction(const T *y0, const T *y1, T h, T r_stop)
 {
     T lo = T(0), hi = T(1);
     T f_lo = y0[1] - r_stop;
-    for (int it = 0; it < BisectIters<T>::value; ++it) {
-        T mid = T(0.5) * (lo + hi);
-        T f_mid = hermite(y0[1], y0[5], y1[1], y1[5], h, mid) - r_stop;
-        if ((f_mid > T(0)) == (f_lo > T(0))) {
-            lo = mid;
-            f_lo = f_mid;
-        } else {
-            hi = mid;
+    if (sizeof(T) == 8) {
+        for (int it = 0; it < BisectIters<T>::value; ++it) {
+            T mid = T(0.5) * (lo + hi);
+            T f_mid = hermite(y0[1], y0[5], y1[1], y1[5], h, mid) - r_stop;
+            if ((f_mid > T(0)) == (f_lo > T(0))) {
+                lo = mid;
+                f_lo = f_mid;
+            } else {
+                hi = mid;
+            }
         }
+        return T(0.5) * (lo + hi);
     }
-    const T s = T(0.5) * (lo + hi);
+    const T f_hi = y1[1] - r_stop;
+    T s = f_lo / (f_lo - f_hi);
+    if (!(s > T(0) && s < T(1)))
+        s = T(0.5);
+    const T p0 = y0[1], m0 = h * y0[5], p1 = y1[1], m1 = h * y1[5];
+    for (int it = 0; it < 6; ++it) {
+        const T s2 = s * s;
+        const T f = hermite(p0, y0[5], p1, y1[5], h, s) - r_stop;
+        const T df = (T(6) * s2 - T(6) * s) * p0 + (T(3) * s2 - T(4) * s + T(1)) * m0 + (T(6) * s - T(6) * s2) * p1 +
+                     (T(3) * s2 - T(2) * s) * m1;
+        if ((f > T(0)) == (f_lo > T(0)))
+            lo = s;
+        else
+            hi = s;
+        T sn = s - f / df;
+        if (!(sn > lo && sn < hi))
+            sn = T(0.5) * (lo + hi);
+        s = sn;
+    }
+    return s;
+}
+
+// Final (t, r, theta, phi) on the stop surface r = r_stop: the crossing
+// fraction, Hermite for the other coordinates, then the pole remap of Eq. 3
+// applied to the interpolated point.
+template <typename T>
+__device__ inline void stop_surface(const T *y0, const T *y1, T h, T r_stop, T *fin)
+{
+    const T s = crossing_fraction(y0, y1, h, r_stop);
     for (int m = 0; m < 4; ++m)
         fin[m] = hermite(y0[m], y0[4 + m], y1[m], y1[4 + m], h, s);
     if (fin[2] > pi_v<T>()) {

@@ -104,7 +104,10 @@ def lib():
     L.gray_setup_noalloc.restype = C.c_int
     L.gray_setup_rays.argtypes = [vp, vp, i64, C.c_double, vp, sz, i64, i64, vp]
     L.gray_setup_rays.restype = C.c_int
-    L.gray_trace.argtypes = [vp, vp, sz, i64, i64, C.POINTER(i64), C.POINTER(i64), vp]
+    L.gray_trace.argtypes = [vp, vp, sz, i64, vp, i64, i64, C.POINTER(i64), C.POINTER(i64), vp]
+    L.gray_trace.restype = C.c_int
+    L.gray_plan.argtypes = [vp, vp, sz, i64, C.POINTER(_Image), i32, i64, i32, i32, vp, sz, vp]
+    L.gray_plan.restype = C.c_int
     L.gray_trace.restype = C.c_int
     L.gray_render.argtypes = [vp, vp, sz, i64, i64, i64, i32, vp, sz, vp]
     L.gray_render.restype = C.c_int
@@ -210,18 +213,35 @@ def gray_setup_rays(ctx, rays, M, state, n_state, first_ray=0, stream=None):
                                         _stream(stream)), "gray_setup_rays")
 
 
-def gray_trace(ctx, state, n_state, step_budget=0, wait=True, stream=None):
+def gray_trace(ctx, state, n_state, step_budget=0, wait=True, stream=None, order=None):
     """Returns (rc, n_active, stats) with stats = (steps, euler, fp64 steps,
-    active) of this call; n_active and stats are None when wait=False."""
+    active) of this call; n_active and stats are None when wait=False.
+    ``order``: optional int32 CUDA tensor, the work queue of ray indices."""
+    op = _ptr(order) if order is not None else None
+    no = order.numel() if order is not None else 0
     if wait:
         na = C.c_int64()
         st = (C.c_int64 * 4)()
-        rc = _check(lib().gray_trace(ctx, _ptr(state), state.numel() * state.element_size(), int(n_state),
+        rc = _check(lib().gray_trace(ctx, _ptr(state), state.numel() * state.element_size(), int(n_state), op, no,
                                      int(step_budget), C.byref(na), st, _stream(stream)), "gray_trace")
         return rc, int(na.value), tuple(int(x) for x in st)
-    rc = _check(lib().gray_trace(ctx, _ptr(state), state.numel() * state.element_size(), int(n_state),
+    rc = _check(lib().gray_trace(ctx, _ptr(state), state.numel() * state.element_size(), int(n_state), op, no,
                                  int(step_budget), None, None, _stream(stream)), "gray_trace")
     return rc, None, None
+
+
+def gray_plan(ctx, state, n_state, images, first_ray=0, probe_stride=4, probe_budget=400, order=None, stream=None):
+    """Longest-first work queue (int32 CUDA tensor) for the rays of ``images``
+    set up at ``first_ray``; the probe rays advance by up to probe_budget."""
+    import torch
+    arr = _images(images)
+    total = sum(int(im.nx) * int(im.ny) for im in images)
+    if order is None:
+        order = torch.empty(max(1, total), dtype=torch.int32, device=state.device)
+    _check(lib().gray_plan(ctx, _ptr(state), state.numel() * state.element_size(), int(n_state), arr, len(images),
+                           int(first_ray), int(probe_stride), int(probe_budget), _ptr(order),
+                           order.numel() * order.element_size(), _stream(stream)), "gray_plan")
+    return order[:total]
 
 
 _PER = {RENDER_PIXELS64: 32, RENDER_PIXELS32: 16, RENDER_RECORD: 17 * 8, RENDER_INVARIANTS: 4 * 8}
@@ -283,7 +303,7 @@ class Tracer:
         self.n = int(n_state)
         self.ctx = gray_create(opt)
         nbytes = gray_state_bytes(self.n, opt.precision)
-        self.state = torch.empty(max(256, nbytes), dtype=torch.uint8, device=device)
+        self.state = torch.zeros(max(256, nbytes), dtype=torch.uint8, device=device)
 
     def close(self):
         if self.ctx is not None:
@@ -302,8 +322,11 @@ class Tracer:
     def setup_rays(self, rays, M=1.0, first_ray=0, stream=None):
         return gray_setup_rays(self.ctx, rays, M, self.state, self.n, first_ray, stream)
 
-    def trace(self, step_budget=0, wait=True, stream=None):
-        return gray_trace(self.ctx, self.state, self.n, step_budget, wait, stream)
+    def trace(self, step_budget=0, wait=True, stream=None, order=None):
+        return gray_trace(self.ctx, self.state, self.n, step_budget, wait, stream, order)
+
+    def plan(self, images, first_ray=0, probe_stride=4, probe_budget=400, order=None, stream=None):
+        return gray_plan(self.ctx, self.state, self.n, images, first_ray, probe_stride, probe_budget, order, stream)
 
     def render(self, kind, first_ray=0, n=None, out=None, stream=None):
         return gray_render(self.ctx, self.state, self.n, kind, first_ray, n, out, stream)

@@ -37,7 +37,7 @@ def test_state_bytes(L):
         b1 = gray.gray_state_bytes(1, prec)
         assert b1 > 0 and b1 % 256 == 0
         n = 1 << 20
-        per = (32 * 3 if prec == gray.FP64 else 16 * 5) + 32 + 16 + 16 + 4
+        per = (32 * 3 if prec == gray.FP64 else 16 * 5 + 32) + 32 + 16 + 16 + 4
         assert gray.gray_state_bytes(n, prec) == per * n
     assert gray.gray_state_bytes(-1, gray.FP64) == 0
     assert gray.gray_state_bytes(10, 7) == 0
@@ -65,7 +65,8 @@ def test_create_rejects_bad_options_before_touching_the_device(L, bad):
 
 def test_calls_reject_null_context(L):
     assert L.gray_setup(None, None, 1, None, 0, 1, 0, None) == gray.EINVAL
-    assert L.gray_trace(None, None, 0, 0, 0, None, None, None) == gray.EINVAL
+    assert L.gray_trace(None, None, 0, 0, None, 0, 0, None, None, None) == gray.EINVAL
+    assert L.gray_plan(None, None, 0, 0, None, 0, 0, 4, 100, None, 0, None) == gray.EINVAL
     assert L.gray_render(None, None, 0, 0, 0, 0, 0, None, 0, None) == gray.EINVAL
     assert L.gray_shadow(None, None, 0, 0, 0, None, 0, None, 0, None) == gray.EINVAL
 
