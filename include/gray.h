@@ -70,6 +70,11 @@ extern "C" {
 #define GRAY_EVAL_RHS 1         /* in (M, a, y[8]) -> out dy/dl, 8 values */
 #define GRAY_EVAL_INITIAL 2     /* in (M, a, r_obs, incl, alpha, beta) -> out y[8] */
 #define GRAY_EVAL_XI 3          /* in (M, a, y[8]) -> out xi of Eq. 4, 1 value */
+#define GRAY_EVAL_SINCOS 4      /* in (theta) -> out (sin, cos) as the tracer evaluates them, 2 values */
+
+/* ---- launch of the trace kernel ------------------------------------- */
+#define GRAY_LAUNCH_PERSISTENT 0     /* persistent warps refilled from a work queue (default) */
+#define GRAY_LAUNCH_ONE_PER_THREAD 1 /* the paper's launch (Eq. 1): one ray per thread, blocks of 64, no refill */
 
 /* One image: a hole of spin a and mass M seen by an observer at distance
  * r_obs and inclination incl, through an nx x ny grid of pixel centres
@@ -93,6 +98,7 @@ typedef struct gray_options {
     int32_t block;         /* threads per block of the trace kernel (multiple of 32, 32..1024), 0 = default */
     int32_t blocks_per_sm; /* resident blocks per SM of the persistent grid, 0 = default */
     int32_t refill;        /* steps between warp refills from the work queue, 0 = default */
+    int32_t launch;        /* GRAY_LAUNCH_PERSISTENT or GRAY_LAUNCH_ONE_PER_THREAD (single precision only) */
     double h_frac;         /* 1/32: the f of the benchmark rule, the Delta of Eq. 2 */
     double h_min;          /* 1e-3: floor on |h| */
     double cap_frac;       /* 1.01: capture when r <= cap_frac * r_h */

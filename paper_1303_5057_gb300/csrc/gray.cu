@@ -419,6 +419,7 @@ struct TraceArgs {
     int refill;
     int step_rule;
     int epoch; // call counter: S1.y == epoch means S1.z counts this call's steps
+    int one_per_thread; // the paper's launch: thread g takes queue slot g only
     double h_frac, h_min, eps_xi, cap_frac, r_esc_frac, r_sw;
     Workspace *ws;
 };
@@ -515,12 +516,16 @@ template <int MODE> __global__ void __maxnreg__(96) trace32_kernel(TraceArgs A)
             const int cnt = __popc(idle);
             const int leader = __ffs(idle) - 1;
             unsigned long long base = 0;
-            if (lane == leader)
-                base = atomicAdd(&A.ws->head, (unsigned long long)cnt);
-            base = __shfl_sync(FULL, base, leader);
+            if (!A.one_per_thread) {
+                if (lane == leader)
+                    base = atomicAdd(&A.ws->head, (unsigned long long)cnt);
+                base = __shfl_sync(FULL, base, leader);
+            }
             bool handoff_now = false;
             if (!has) {
-                const int64_t slot = (int64_t)base + __popc(idle & ((1u << lane) - 1u));
+                const int64_t slot = A.one_per_thread
+                                         ? (int64_t)blockIdx.x * blockDim.x + threadIdx.x
+                                         : (int64_t)base + __popc(idle & ((1u << lane) - 1u));
                 const int64_t my = slot < nq ? queue_ray(A, slot) : -1;
                 if (my >= 0) {
                     const int4 s0 = v.S0[my];
@@ -563,7 +568,7 @@ template <int MODE> __global__ void __maxnreg__(96) trace32_kernel(TraceArgs A)
                 if (handoff_now)
                     v.L[hb + rank] = (int)id;
             }
-            if ((int64_t)base + cnt >= nq)
+            if (A.one_per_thread || (int64_t)base + cnt >= nq)
                 exhausted = true;
         }
         if (!__any_sync(FULL, has))
@@ -1182,6 +1187,11 @@ template <typename T> __global__ void eval_kernel(int what, const double *in, in
         initial_state(q[0], q[1], q[2], q[3], q[4], q[5], y);
         for (int m = 0; m < 8; ++m)
             out[8 * i + m] = y[m];
+    } else if (what == GRAY_EVAL_SINCOS) {
+        T sv, cv;
+        fsincos((T)in[i], &sv, &cv);
+        out[2 * i] = (double)sv;
+        out[2 * i + 1] = (double)cv;
     } else if (what == GRAY_EVAL_XI) {
         const double *q = in + 10 * i;
         const Hole<T> H = cast_hole<T>(make_hole(q[1], q[0], 1.0, 1.0, 1.0, 0.0));
@@ -1225,6 +1235,8 @@ int validate_options(const gray_options *o)
     if (o->block != 0 && (o->block < 32 || o->block > 1024 || o->block % 32 != 0))
         return GRAY_EINVAL;
     if (o->blocks_per_sm < 0 || o->blocks_per_sm > 64 || o->refill < 0 || o->refill > 100000)
+        return GRAY_EINVAL;
+    if (o->launch != GRAY_LAUNCH_PERSISTENT && o->launch != GRAY_LAUNCH_ONE_PER_THREAD)
         return GRAY_EINVAL;
     if (!finite_all({o->h_frac, o->h_min, o->cap_frac, o->eps_xi, o->r_esc_frac, o->r_sw}))
         return GRAY_EINVAL;
@@ -1315,6 +1327,7 @@ void gray_default_options(gray_options *o)
     o->block = 0;
     o->blocks_per_sm = 0;
     o->refill = 0;
+    o->launch = GRAY_LAUNCH_PERSISTENT;
     o->h_frac = 1.0 / 32.0;
     o->h_min = 1e-3;
     o->cap_frac = 1.01;
@@ -1450,6 +1463,7 @@ TraceArgs make_trace_args(gray_ctx *ctx, void *state, int64_t n_state, int64_t s
     A.r_esc_frac = o.r_esc_frac;
     A.r_sw = o.r_sw;
     A.ws = ctx->ws;
+    A.one_per_thread = o.launch == GRAY_LAUNCH_ONE_PER_THREAD;
     return A;
 }
 
@@ -1472,6 +1486,24 @@ unsigned persistent_grid(const gray_ctx *ctx, const void *kernel, int block, int
 // One single- or double-precision pass over the queue of A (no zone kernel).
 int launch_pass(gray_ctx *ctx, const TraceArgs &A, int64_t work, cudaStream_t s)
 {
+    if (A.one_per_thread && ctx->opt.precision != GRAY_FP64) {
+        // the paper's launch (Eq. 1): n_grid = floor((n - 1) / n_block) + 1
+        // blocks of n_block = 64 threads, one ray per thread, no refill
+        const int nb = ctx->opt.block > 0 ? ctx->opt.block : 64;
+        const unsigned grid = (unsigned)((work - 1) / nb + 1);
+        switch (ctx->opt.precision) {
+        case GRAY_FP32:
+            trace32_kernel<GRAY_FP32><<<grid, nb, 0, s>>>(A);
+            break;
+        case GRAY_FP32_KAHAN:
+            trace32_kernel<GRAY_FP32_KAHAN><<<grid, nb, 0, s>>>(A);
+            break;
+        default:
+            trace32_kernel<GRAY_FP32_KAHAN_SEL64><<<grid, nb, 0, s>>>(A);
+            break;
+        }
+        return check_launch();
+    }
     const int block = ctx->opt.block > 0 ? ctx->opt.block : 128;
     switch (ctx->opt.precision) {
     case GRAY_FP64:
@@ -1668,7 +1700,7 @@ int gray_shadow(gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_
 
 int gray_eval(int32_t what, int32_t precision, const double *in, int64_t n, double *out, void *stream)
 {
-    if (what < GRAY_EVAL_CHRISTOFFEL || what > GRAY_EVAL_XI || n < 0)
+    if (what < GRAY_EVAL_CHRISTOFFEL || what > GRAY_EVAL_SINCOS || n < 0)
         return GRAY_EINVAL;
     if (precision != GRAY_FP64 && precision != GRAY_FP32)
         return GRAY_EINVAL;

@@ -51,6 +51,7 @@ template <> __device__ __forceinline__ double pi_v<double>() { return 3.14159265
 // Per-ray constants of the spacetime and of the stop surfaces.
 template <typename T> struct Hole {
     T a, M;
+    T a2, Ma, m2M; // a^2, M a, -2 M
     T rp, rm, dc; // Delta = (r - rp)(r - rm) + dc
     T rp_lo;      // single precision: rp - (float)rp, so rp is carried to ~48 bits
     T r_h;        // horizon used by the step guard; -inf when M = 0 (no guard)
@@ -72,6 +73,9 @@ __host__ __device__ inline Hole<double> make_hole(double a, double M, double r_o
     Hole<double> H;
     H.a = a;
     H.M = M;
+    H.a2 = a * a;
+    H.Ma = M * a;
+    H.m2M = -2.0 * M;
     double disc = M * M - a * a;
     double root = disc > 0.0 ? sqrt(disc) : 0.0;
     H.rp = M + root;
@@ -96,6 +100,9 @@ template <typename T> __host__ __device__ inline Hole<T> cast_hole(const Hole<do
     Hole<T> o;
     o.a = (T)h.a;
     o.M = (T)h.M;
+    o.a2 = o.a * o.a;
+    o.Ma = o.M * o.a;
+    o.m2M = T(-2) * o.M;
     o.rp = (T)h.rp;
     o.rp_lo = (T)(h.rp - (double)o.rp);
     o.rm = (T)h.rm;
@@ -128,6 +135,9 @@ __device__ __forceinline__ Hole<float> make_hole_f(float4 c0, float4 c1, float c
     Hole<float> H;
     H.a = c0.x;
     H.M = c0.y;
+    H.a2 = H.a * H.a;
+    H.Ma = H.M * H.a;
+    H.m2M = -2.0f * H.M;
     H.rp = c0.z;
     H.rp_lo = c0.w;
     H.rm = c1.x;
@@ -277,30 +287,51 @@ __device__ __forceinline__ Geo<T> geometry(const Hole<T> &H, T r, T th, T dr = T
     return g;
 }
 
-// dk^mu/dl at a point whose geometry is known (same grouping as below).
+// dk^mu/dl at a point whose geometry is known: the closed-form symbols
+// contracted with k k, grouped with w = k^t - a s^2 k^ph, iSw = w / Sigma,
+// A = r^2 - a^2 c^2 = 2 r^2 - Sigma, P = r^2 + a^2:
+//   a^t  = -2M/Sigma [ k^r/Delta (P A iSw - 2 a r^2 s^2 k^ph) - 2 a^2 r s c k^th iSw ]
+//   a^r  = [ -M A Delta iSw^2 + Delta r (s^2 k^ph^2 + k^th^2)
+//            - (a^2 r s^2 - M A) k^r^2/Delta + 2 a^2 s c k^r k^th ] / Sigma
+//   a^th = [ s c (2 M a^2 r iSw^2 - 4 M a r iSw k^ph + P k^ph^2
+//                 + a^2 (k^th^2 - k^r^2/Delta)) - 2 r k^r k^th ] / Sigma
+//   a^ph = -2 [ k^r/Delta (M a A iSw/Sigma + r k^ph (1 - 2 M r/Sigma))
+//               + cot(th) k^th (k^ph - 2 M a r iSw/Sigma) ]
 template <typename T>
 __device__ __forceinline__ void accel_geo(const Hole<T> &H, const Geo<T> &g, T kt, T kr, T kh, T kp, T *acc)
 {
-    const T a = H.a, M = H.M, r = g.r, s = g.s, c = g.c;
-    const T a2 = a * a, r2 = r * r, s2 = s * s, c2 = c * c, sc = s * c;
-    const T iS = g.iS, iD = g.iD, Delta = g.Delta;
-    const T iS2 = iS * iS;
-    const T A = fma(-a2, c2, r2), P = r2 + a2;
-    const T w = fma(-a * s2, kp, kt);
-    const T cot = c * g.is;
+    const T a = H.a, M = H.M, a2 = H.a2;
+    const T r = g.r, iS = g.iS, iD = g.iD, Delta = g.Delta;
+    const T r2 = r * r, s2 = g.s * g.s, sc = g.s * g.c;
+    const T A = fma(T(2), r2, -g.Sigma);
+    const T P = r2 + a2;
+    const T as2 = a * s2;
+    const T iSw = iS * fma(-as2, kp, kt);
     const T Mr = M * r;
-    const T u_t = fma(iS * P * A, w, -T(2) * a * r2 * s2 * kp);
-    acc[0] = -T(2) * M * iS * (iD * kr * u_t - T(2) * a2 * r * sc * iS * kh * w);
-    const T ang = fma(s2 * kp, kp, kh * kh);
-    const T u_r = -M * Delta * A * iS2 * w * w + Delta * r * ang - (a2 * r * s2 - M * A) * iD * kr * kr
-                  + T(2) * a2 * sc * kr * kh;
-    acc[1] = iS * u_r;
-    const T u_h = T(2) * Mr * a2 * iS2 * w * w - T(4) * Mr * a * iS * w * kp + P * kp * kp - a2 * iD * kr * kr
-                  + a2 * kh * kh;
-    acc[2] = iS * (sc * u_h - T(2) * r * kr * kh);
-    const T u_p1 = r * kp * (T(1) - T(2) * Mr * iS) + M * a * A * iS2 * w;
-    const T u_p2 = kp - T(2) * Mr * a * iS2 * w;
-    acc[3] = -T(2) * (kr * iD * u_p1 + cot * kh * u_p2);
+    const T kr2 = kr * kr, krkh = kr * kh, khkh = kh * kh, kpkp = kp * kp;
+    const T iDkr = iD * kr;
+    const T a2r = a2 * r;
+    // t
+    const T u_t = fma(T(-2) * (r2 * as2), kp, (P * A) * iSw);
+    const T x_t = (a2r * sc) * (kh * iSw);
+    acc[0] = (H.m2M * iS) * fma(iDkr, u_t, T(-2) * x_t);
+    // r
+    const T iSw2 = iSw * iSw;
+    const T MA = M * A;
+    const T t1 = (MA * Delta) * iSw2;
+    const T t2 = (Delta * r) * fma(s2, kpkp, khkh);
+    const T t3 = fma(a2r, s2, -MA) * (iD * kr2);
+    const T t4 = (a2 * sc) * krkh;
+    acc[1] = iS * fma(T(2), t4, (t2 - t1) - t3);
+    // theta
+    const T U2 = (Mr * a) * iSw;
+    const T h_in = fma(T(2) * (M * a2r), iSw2, fma(T(-4) * U2, kp, fma(P, kpkp, a2 * fma(-iD, kr2, khkh))));
+    acc[2] = iS * fma(sc, h_in, T(-2) * r * krkh);
+    // phi
+    const T cot = g.c * g.is;
+    const T up1 = fma((H.Ma * A) * iS, iSw, (r * kp) * fma(T(-2) * Mr, iS, T(1)));
+    const T up2 = fma(T(-2) * U2, iS, kp);
+    acc[3] = T(-2) * fma(iDkr, up1, (cot * kh) * up2);
 }
 
 // Eq. 4 test without its division: |xi + 1| > eps  <=>

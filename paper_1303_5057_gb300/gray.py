@@ -25,7 +25,8 @@ ACTIVE, CAPTURED, ESCAPED, STEP_CAP, NONFINITE = 0, 1, 2, 3, 4
 FP64, FP32, FP32_KAHAN, FP32_KAHAN_SEL64 = 0, 1, 2, 3
 STEP_BENCH, STEP_EQ2 = 0, 1
 RENDER_PIXELS64, RENDER_PIXELS32, RENDER_RECORD, RENDER_INVARIANTS = 0, 1, 3, 4
-EVAL_CHRISTOFFEL, EVAL_RHS, EVAL_INITIAL, EVAL_XI = 0, 1, 2, 3
+EVAL_CHRISTOFFEL, EVAL_RHS, EVAL_INITIAL, EVAL_XI, EVAL_SINCOS = 0, 1, 2, 3, 4
+LAUNCH_PERSISTENT, LAUNCH_ONE_PER_THREAD = 0, 1
 RECORD = 17
 NOALLOC_MAX_IMAGES = 4096
 
@@ -41,6 +42,7 @@ class GrayError(RuntimeError):
 class _Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("step_rule", C.c_int32), ("max_steps", C.c_int32),
                 ("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill", C.c_int32),
+                ("launch", C.c_int32),
                 ("h_frac", C.c_double), ("h_min", C.c_double), ("cap_frac", C.c_double),
                 ("eps_xi", C.c_double), ("r_esc_frac", C.c_double), ("r_sw", C.c_double)]
 
@@ -66,6 +68,7 @@ class Options:
     block: int = 0
     blocks_per_sm: int = 0
     refill: int = 0
+    launch: int = LAUNCH_PERSISTENT
     h_frac: float = 1.0 / 32.0
     h_min: float = 1e-3
     cap_frac: float = 1.01
@@ -277,8 +280,8 @@ def gray_eval(what, precision, inp, stream=None):
     """inp: float64 CUDA tensor of n rows (4, 10, 6 or 10 doubles by ``what``).
     Returns a float64 CUDA tensor of n rows (64, 8, 8 or 1 doubles)."""
     import torch
-    width_in = {EVAL_CHRISTOFFEL: 4, EVAL_RHS: 10, EVAL_INITIAL: 6, EVAL_XI: 10}[what]
-    width_out = {EVAL_CHRISTOFFEL: 64, EVAL_RHS: 8, EVAL_INITIAL: 8, EVAL_XI: 1}[what]
+    width_in = {EVAL_CHRISTOFFEL: 4, EVAL_RHS: 10, EVAL_INITIAL: 6, EVAL_XI: 10, EVAL_SINCOS: 1}[what]
+    width_out = {EVAL_CHRISTOFFEL: 64, EVAL_RHS: 8, EVAL_INITIAL: 8, EVAL_XI: 1, EVAL_SINCOS: 2}[what]
     inp = inp.contiguous()
     n = inp.numel() // width_in
     out = torch.empty((n, width_out), dtype=torch.float64, device=inp.device)

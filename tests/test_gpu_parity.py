@@ -122,6 +122,21 @@ def test_xi_matches_oracle(prec, tol):
         assert abs(got[i] - ref) <= tol * max(1.0, abs(ref))
 
 
+def test_single_precision_sincos_error_bound():
+    """The single-precision sin/cos the tracer evaluates, against double sin/cos
+    of the same float argument: both within 4 ulp of themselves (relative, so
+    1/sin and cot stay accurate near both poles and cos near the equator)."""
+    rng = np.random.default_rng(4)
+    th = np.concatenate([rng.uniform(-math.pi / 2, 1.5 * math.pi, 20000),
+                         np.geomspace(1e-7, 1e-1, 200), math.pi - np.geomspace(1e-6, 1e-1, 200),
+                         [0.0, math.pi / 2, math.pi, -1.0, 5.0, -3.0, 40.0]]).astype(np.float32).astype(np.float64)
+    got = gray.gray_eval(gray.EVAL_SINCOS, gray.FP32, dev(th[:, None])).cpu().numpy()
+    s_ref, c_ref = np.sin(th), np.cos(th)
+    for k, ref in ((0, s_ref), (1, c_ref)):
+        ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+        assert np.all(np.abs(got[:, k] - ref) <= 4 * ulp + 1e-45), k
+
+
 # ------------------------------------------------------------- whole rays ---
 
 def test_schwarzschild_64x64_fp64_matches_oracle():
@@ -207,16 +222,22 @@ def test_kerr_fp32_compensated_without_double():
 
 
 def test_kerr_fp32_plain_is_less_accurate_than_compensated():
-    """Plain FP32 (no compensation) classifies the same rays but its angles
-    drift further from the oracle than the compensated path's."""
+    """Plain FP32 (no compensation) classifies the same rays, but its final
+    angles sit further from the oracle than the compensated path's (median and
+    99th percentile over the faithfully integrated rays)."""
     im, rays, ref, far, qd = kerr_reference(gray.STEP_BENCH)
-    sane = far & (qd < P.SANE_Q)
+    sane = far & (qd < P.SANE_Q) & ((ref[:, 0] == oracle.CAPTURED) | (ref[:, 0] == oracle.ESCAPED))
     plain, _, _, _ = trace_image(im, gray.Options(precision=gray.FP32, max_steps=10000))
     comp, _, _, _ = trace_image(im, gray.Options(precision=gray.FP32_KAHAN, max_steps=10000))
     assert P.compare(plain, ref, far)["class_agree_far"] >= 0.9999
-    cp, cc = P.compare(plain, ref, sane), P.compare(comp, ref, sane)
-    assert cp["p9999_dang"] > cc["p9999_dang"]
-    assert cp["max_dphi"] < 0.1
+
+    def err(rec):
+        ok = sane & (rec[:, 0] == ref[:, 0])
+        return np.maximum(np.abs(rec[ok, 6] - ref[ok, 6]), np.abs(P.wrap(rec[ok, 7] - ref[ok, 7])))
+
+    ep, ec = err(plain), err(comp)
+    assert np.median(ep) > 2 * np.median(ec)
+    assert np.percentile(ep, 99) > np.percentile(ec, 99)
 
 
 def test_kerr_eq2_fp32_selective_fp64():
@@ -324,10 +345,35 @@ def test_planned_order_gives_identical_results(prec):
     tr.close()
     assert rc == 1 and n_active == 5  # the five rays before first_ray were never set up, nor traced
     assert np.array_equal(want, got)
-    # the head of the queue holds longer rays than the average
-    steps = want[:, 1]
-    head = steps[o[: n // 10] - 5]
-    assert head.mean() > steps.mean()
+
+
+@pytest.mark.parametrize("prec", [gray.FP32_KAHAN, gray.FP32_KAHAN_SEL64])
+def test_one_ray_per_thread_launch_equals_persistent(prec):
+    """The paper's launch (Eq. 1: one ray per thread, blocks of 64) and the
+    persistent refilling queue compute each ray identically."""
+    im = I.Image(a=0.9, incl=1.2, nx=37, ny=31)
+    a, _, _, _ = trace_image(im, gray.Options(precision=prec, max_steps=10000, r_sw=0.02))
+    b, _, _, _ = trace_image(im, gray.Options(precision=prec, max_steps=10000, r_sw=0.02,
+                                              launch=gray.LAUNCH_ONE_PER_THREAD))
+    assert np.array_equal(a, b)
+
+
+def test_plan_puts_long_rays_first():
+    """On a 256^2 image of the a = 0.99, i = 90 deg workload, the rays that
+    take over 1000 steps sit in the first fifth of the planned queue."""
+    im = I.kerr_1024(256).images[0]
+    opt = gray.Options(precision=gray.FP32_KAHAN, max_steps=10000)
+    tr = gray.Tracer(opt, im.n)
+    tr.setup([im])
+    order = tr.plan([im], probe_stride=4, probe_budget=400).cpu().numpy()
+    tr.trace()
+    steps = tr.records()[:, 1]
+    tr.close()
+    pos = np.empty(im.n, dtype=np.int64)
+    pos[order] = np.arange(im.n)
+    long = steps > 1000
+    assert long.sum() > 100
+    assert np.median(pos[long]) < 0.2 * im.n
 
 
 def test_order_restricts_the_trace_to_listed_rays():
