@@ -65,6 +65,12 @@ def parse_args():
     p.add_argument("--no-fp64-leg", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-rays", type=int, default=16384)
+    p.add_argument("--workload", default="kerr1024",
+                   choices=["kerr1024", "schwarzschild64", "mixed", "sweep", "serve"])
+    p.add_argument("--rays", type=int, default=1 << 22, help="mixed workload: rays")
+    p.add_argument("--images", type=int, default=256, help="sweep workload: images")
+    p.add_argument("--rates", default="10,30,100,300,1000", help="serve workload: req/s")
+    p.add_argument("--requests", type=int, default=200, help="serve workload: requests per rate")
     return p.parse_args()
 
 
@@ -174,12 +180,151 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------- other workloads (GPU) ---
+
+def _timed(fn, repeats):
+    import torch
+    ts = []
+    for _ in range(repeats):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return min(ts), out
+
+
+def run_schwarzschild64(args):
+    """a = 0, i = 60 deg, 64 x 64, FP64 on the GPU against the FP64 oracle on
+    the host cores (the whole image both ways)."""
+    import torch
+    import oracle
+    from paper_1303_5057_gb300 import gray
+    from paper_1303_5057_gb300 import inputs as I
+    wl = I.schwarzschild_64()
+    im = wl.images[0]
+    tr = gray.Tracer(gray.Options(precision=gray.FP64, max_steps=wl.max_steps), im.n)
+
+    def step():
+        tr.setup([im])
+        return tr.trace()[2]
+    step()
+    ms, st = _timed(step, max(3, args.steps))
+    rays = oracle.image_rays(im.a, im.incl, im.r_obs, im.nx, im.ny, im.alpha0, im.alpha1, im.beta0, im.beta1)
+    t0 = time.perf_counter()
+    out = oracle.trace_many(rays, oracle.Options(max_steps=wl.max_steps))
+    dt = time.perf_counter() - t0
+    tr.close()
+    print(json.dumps({"workload": wl.name, "metric": "photon RK4 steps/s", "unit": UNIT, "dtype": "f64",
+                      "gpu": {"value": st[0] / (ms / 1000.0), "ms_per_image": ms, "steps": st[0]},
+                      "cpu_oracle": {"value": float(out[:, 1].sum()) / dt, "s_per_image": dt,
+                                     "cores": os.cpu_count()}}), flush=True)
+    return 0
+
+
+def run_mixed(args):
+    """2^k rays, per-ray (alpha, beta, a, i), half near each ray's critical
+    curve: the precision variants with the persistent refilling queue
+    (compaction on) and with the paper's one-ray-per-thread launch (off)."""
+    import torch
+    from paper_1303_5057_gb300 import gray
+    from paper_1303_5057_gb300 import inputs as I
+    n = args.rays
+    t0 = time.perf_counter()
+    rays = torch.as_tensor(I.mixed_rays(n), device="cuda")
+    gen_s = time.perf_counter() - t0
+    res = {}
+    variants = [("fp32", gray.FP32, gray.LAUNCH_PERSISTENT), ("fp32_kahan", gray.FP32_KAHAN, gray.LAUNCH_PERSISTENT),
+                ("fp32_kahan_sel64", gray.FP32_KAHAN_SEL64, gray.LAUNCH_PERSISTENT),
+                ("fp32_kahan_sel64_no_compaction", gray.FP32_KAHAN_SEL64, gray.LAUNCH_ONE_PER_THREAD)]
+    for name, prec, launch in variants:
+        tr = gray.Tracer(gray.Options(precision=prec, max_steps=10000, r_sw=args.r_sw, launch=launch), n)
+
+        def step():
+            tr.setup_rays(rays)
+            return tr.trace()[2]
+        step()
+        ms, st = _timed(step, 2)
+        tr.close()
+        res[name] = {"value": st[0] / (ms / 1000.0), "ms": ms, "steps": st[0], "fp64_steps": st[2]}
+    # plain FP64 on a 1/16 subset (1/64 of the FP32 rate)
+    sub = rays[: max(1, n // 16)].contiguous()
+    tr = gray.Tracer(gray.Options(precision=gray.FP64, max_steps=10000), sub.shape[0])
+
+    def step64():
+        tr.setup_rays(sub)
+        return tr.trace()[2]
+    ms, st = _timed(step64, 1)
+    tr.close()
+    res["fp64_subset_1_16"] = {"value": st[0] / (ms / 1000.0), "ms": ms, "steps": st[0]}
+    print(json.dumps({"workload": "mixed_%d_rays" % n, "metric": "photon RK4 steps/s", "unit": UNIT,
+                      "generation_s": gen_s, "variants": res}), flush=True)
+    return 0
+
+
+def run_sweep(args):
+    """Batched shadow sweep: `images` (a, i) images of side U{64..1024} in one
+    set-up, one plan, one persistent trace and one shadow reduction."""
+    import torch
+    from paper_1303_5057_gb300 import batch, gray
+    from paper_1303_5057_gb300 import inputs as I
+    wl = I.shadow_sweep(n_images=args.images)
+    opt = gray.Options(precision=gray.FP32_KAHAN_SEL64, max_steps=10000, r_sw=args.r_sw,
+                       block=args.block, blocks_per_sm=args.blocks_per_sm, refill=args.refill)
+    sw = batch.ShadowSweep(wl.images, opt, plan=not args.no_plan, probe_stride=args.probe_stride,
+                           probe_budget=args.probe_budget)
+    sw.run()
+    times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        sh, ms = sw.run()
+        times.append(ms)
+    steps = int(sw.stats()[:, 1].sum())
+    sw.close()
+    ms = min(times)
+    print(json.dumps({"workload": wl.name, "images": len(wl.images), "rays": wl.n_rays,
+                      "metric": "photon RK4 steps/s", "unit": UNIT, "value": steps / (ms / 1000.0),
+                      "ms_per_sweep": ms, "steps": steps,
+                      "radius_range": [float(sh["radius"].min()), float(sh["radius"].max())],
+                      "queue": "natural" if args.no_plan else "planned"}), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson arrivals of render requests (side in {32, ..., 2048}, a, i
+    random), continuous batching over a resident pool; p50/p99 latency and
+    photon-steps/s per arrival rate."""
+    from paper_1303_5057_gb300 import gray, serve
+    from paper_1303_5057_gb300 import inputs as I
+    opt = gray.Options(precision=gray.FP32_KAHAN_SEL64, max_steps=10000, r_sw=args.r_sw)
+    out = []
+    for rate in [float(x) for x in args.rates.split(",")]:
+        srv = serve.Server(opt, capacity=16 << 20, round_budget=256)
+        reqs = I.request_stream(rate, args.requests)
+        st = srv.run(reqs, realtime=True, max_wall=60.0)
+        srv.close()
+        summ = st.summary()
+        summ["rate_req_per_s"] = rate
+        out.append(summ)
+        print(json.dumps({"workload": "serve", "rate": rate, **summ}), flush=True)
+    return 0
+
+
 # --------------------------------------------------------------- GPU arm ---
 
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "kerr1024":
+        import torch
+        from paper_1303_5057_gb300 import build, gray
+        torch.cuda.set_device(0)
+        build.build()
+        gray.lib()
+        return {"schwarzschild64": run_schwarzschild64, "mixed": run_mixed, "sweep": run_sweep,
+                "serve": run_serve}[args.workload](args)
 
     import torch
 

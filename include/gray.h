@@ -48,6 +48,7 @@ extern "C" {
 #define GRAY_RAY_ESCAPED 2   /* reached r >= r_esc moving outward along the trace */
 #define GRAY_RAY_STEP_CAP 3  /* hit max_steps */
 #define GRAY_RAY_NONFINITE 4 /* state became NaN or Inf */
+#define GRAY_RAY_EMPTY 5     /* an unused slot of a resident pool (gray_clear) */
 
 /* ---- arithmetic of the trace ---------------------------------------- */
 #define GRAY_FP64 0             /* every step in double precision */
@@ -227,6 +228,19 @@ int gray_plan(gray_ctx *ctx, void *state_dev, size_t state_bytes, int64_t n_stat
 int gray_render(gray_ctx *ctx, const void *state_dev, size_t state_bytes, int64_t n_state,
                 int64_t first_ray, int64_t n, int32_t kind, void *out_dev, size_t out_bytes,
                 void *stream);
+
+/* Mark rays first_ray .. first_ray + n - 1 as empty slots (GRAY_RAY_EMPTY):
+ * traces skip them and gray_count_active does not count them.  For resident
+ * pools that admit requests into free slots.  Errors: GRAY_EINVAL, GRAY_ECUDA. */
+int gray_clear(gray_ctx *ctx, void *state_dev, size_t state_bytes, int64_t n_state,
+               int64_t first_ray, int64_t n, void *stream);
+
+/* Number of ACTIVE rays in each of n_ranges ranges of the buffer: ranges_host
+ * holds (first_ray, count) pairs; counts_host receives n_ranges int64.  Waits
+ * for the stream.  Errors: GRAY_EINVAL (range outside the buffer), GRAY_ECUDA. */
+int gray_count_active(gray_ctx *ctx, const void *state_dev, size_t state_bytes, int64_t n_state,
+                      const int64_t *ranges_host, int32_t n_ranges, int64_t *counts_host,
+                      void *stream);
 
 /* Shadow of each of n_images images whose rays start at first_ray (as laid
  * down by gray_setup with the same image list): captured count, area of the

@@ -166,8 +166,7 @@ struct gray_ctx {
     Workspace *ws_host = nullptr; // pinned host mirror
     int device = 0;
     int num_sms = 0;
-    int epoch = 0;                  // gray_trace calls made with this context
-    unsigned long long *aux = nullptr; // device: planning counters and histograms
+    unsigned long long *aux = nullptr; // device: planning counters, histograms, call epoch
 };
 
 namespace {
@@ -418,7 +417,8 @@ struct TraceArgs {
     int max_steps;
     int refill;
     int step_rule;
-    int epoch; // call counter: S1.y == epoch means S1.z counts this call's steps
+    const int *epoch_dev; // call counter on the device (bumped by every gray_trace / gray_plan):
+                          // S1.y == epoch means S1.z counts this call's steps
     int one_per_thread; // the paper's launch: thread g takes queue slot g only
     double h_frac, h_min, eps_xi, cap_frac, r_esc_frac, r_sw;
     Workspace *ws;
@@ -500,6 +500,7 @@ template <int MODE> __global__ void __maxnreg__(96) trace32_kernel(TraceArgs A)
     bool has = false, exhausted = false;
     int64_t id = 0;
     const int64_t nq = queue_length(A);
+    const int epoch = *A.epoch_dev;
     float y[8], c[8], fin[4];
     Hole<float> H;
     Geo<float> geo;
@@ -541,7 +542,7 @@ template <int MODE> __global__ void __maxnreg__(96) trace32_kernel(TraceArgs A)
                             euler = s0.z;
                             remaps = s0.w;
                             n64 = s1.x;
-                            used = (s1.y == A.epoch) ? s1.z : 0;
+                            used = (s1.y == epoch) ? s1.z : 0;
                             H = make_hole_f(v.PF0[my], v.PF1[my], (float)A.cap_frac, (float)A.r_esc_frac,
                                             (float)A.r_sw);
                             r_promote = H.r_promote;
@@ -606,7 +607,7 @@ template <int MODE> __global__ void __maxnreg__(96) trace32_kernel(TraceArgs A)
                     if (status != GRAY_RAY_ACTIVE)
                         st_f4(v.F, id, fin[0], fin[1], fin[2], fin[3]);
                     v.S0[id] = make_int4(status, steps, euler, remaps);
-                    v.S1[id] = make_int4(n64, A.epoch, used, handoff ? FLAG_DOUBLE_MODE : 0);
+                    v.S1[id] = make_int4(n64, epoch, used, handoff ? FLAG_DOUBLE_MODE : 0);
                     has = false;
                 }
             }
@@ -641,6 +642,7 @@ __global__ void __launch_bounds__(128) trace64_kernel(TraceArgs A)
     int steps = 0, euler = 0, remaps = 0, n64 = 0, used = 0;
     unsigned long long tot_steps = 0, tot_euler = 0;
     const int64_t nq = queue_length(A);
+    const int epoch = *A.epoch_dev;
 #pragma unroll
     for (int m = 0; m < 8; ++m)
         cz[m] = 0.0;
@@ -669,7 +671,7 @@ __global__ void __launch_bounds__(128) trace64_kernel(TraceArgs A)
                         euler = s0.z;
                         remaps = s0.w;
                         n64 = s1.x;
-                        used = (s1.y == A.epoch) ? s1.z : 0;
+                        used = (s1.y == epoch) ? s1.z : 0;
                         const d4 p = ld_d4(v.P, my);
                         H = make_hole(p.x, p.y, p.z, A.cap_frac, A.r_esc_frac, A.r_sw);
                         const d4 X = ld_d4(v.X, my), K = ld_d4(v.K, my);
@@ -709,7 +711,7 @@ __global__ void __launch_bounds__(128) trace64_kernel(TraceArgs A)
                     if (status != GRAY_RAY_ACTIVE)
                         st_d4(v.F, id, fin[0], fin[1], fin[2], fin[3]);
                     v.S0[id] = make_int4(status, steps, euler, remaps);
-                    v.S1[id] = make_int4(n64, A.epoch, used, 0);
+                    v.S1[id] = make_int4(n64, epoch, used, 0);
                     has = false;
                 }
             }
@@ -740,6 +742,7 @@ __global__ void __launch_bounds__(128, 1) zone_kernel(TraceArgs A)
     Of.eps_xi = (float)A.eps_xi;
     Of.step_rule = A.step_rule;
     const int64_t n = (int64_t)*(volatile unsigned long long *)&A.ws->handoff;
+    const int epoch = *A.epoch_dev;
 
     bool has = false, exhausted = false, dbl = true;
     int64_t id = 0;
@@ -781,7 +784,7 @@ __global__ void __launch_bounds__(128, 1) zone_kernel(TraceArgs A)
                         euler = s0.z;
                         remaps = s0.w;
                         n64 = s1.x;
-                        used = (s1.y == A.epoch) ? s1.z : 0;
+                        used = (s1.y == epoch) ? s1.z : 0;
                         const d4 p = ld_d4(v.P, my);
                         Hd = make_hole(p.x, p.y, p.z, A.cap_frac, A.r_esc_frac, A.r_sw);
                         Hf = make_hole_f(v.PF0[my], v.PF1[my], (float)A.cap_frac, (float)A.r_esc_frac,
@@ -880,11 +883,43 @@ __global__ void __launch_bounds__(128, 1) zone_kernel(TraceArgs A)
                     st_f4(v.F, id, (float)find[0], (float)find[1], (float)find[2], (float)find[3]);
             }
             v.S0[id] = make_int4(status, steps, euler, remaps);
-            v.S1[id] = make_int4(n64, A.epoch, used, flags);
+            v.S1[id] = make_int4(n64, epoch, used, flags);
             has = false;
         }
     }
     warp_stats<double>(A, lane, tot_steps, tot_euler, tot_fp64);
+}
+
+// Mark rays as empty slots (never traced, never counted as active).
+__global__ void clear_kernel(StateView v, int64_t first, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    v.S0[first + i] = make_int4(GRAY_RAY_EMPTY, 0, 0, 0);
+    v.S1[first + i] = make_int4(0, 0, 0, 0);
+}
+
+// ACTIVE rays of each range (first, count): one block per range.
+__global__ void count_ranges_kernel(const int4 *S0, const long long *ranges, unsigned long long *counts)
+{
+    const long long first = ranges[2 * blockIdx.x], len = ranges[2 * blockIdx.x + 1];
+    unsigned long long mine = 0;
+    for (long long i = threadIdx.x; i < len; i += blockDim.x)
+        mine += (S0[first + i].x == GRAY_RAY_ACTIVE);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+        mine += __shfl_xor_sync(0xffffffffu, mine, off);
+    __shared__ unsigned long long part[32];
+    if ((threadIdx.x & 31) == 0)
+        part[threadIdx.x >> 5] = mine;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            t += part[w];
+        counts[blockIdx.x] = t;
+    }
 }
 
 // Rays still ACTIVE (for the per-call statistics).
@@ -918,6 +953,15 @@ __global__ void count_active_kernel(const int4 *S0, int64_t n, unsigned long lon
 constexpr int PLAN_BUCKETS = 64;
 // aux layout: [0] probe count, [1..64] histogram, [65..128] bucket offsets
 constexpr int AUX_PROBES = 0, AUX_HIST = 1, AUX_OFF = 1 + PLAN_BUCKETS, AUX_WORDS = 1 + 2 * PLAN_BUCKETS;
+// one more word after the planning words: the call epoch (never cleared)
+constexpr int AUX_EPOCH = AUX_WORDS, AUX_ALLOC = AUX_WORDS + 1;
+
+// Start a new call: epochs run 1 .. 2^31 - 2 (0 marks a ray no call touched).
+__global__ void bump_epoch_kernel(unsigned long long *aux)
+{
+    int *e = (int *)&aux[AUX_EPOCH];
+    *e = (*e % 0x7ffffffe) + 1;
+}
 
 __device__ __forceinline__ int image_of(const ImageDev *imgs, int n_images, int64_t i)
 {
@@ -1105,8 +1149,10 @@ __global__ void render_kernel(StateView v, int prec, int64_t first, int64_t n, i
     }
 }
 
-// Shadow moments: counts and sum of (alpha, beta) of captured pixels per image,
-// accumulated directly in the caller's output records, then finalised.
+// Shadow moments: counts and the sums of the captured pixels' column and row
+// indices per image, accumulated as 64-bit integers (exact, independent of
+// the order of the atomics) directly in the caller's output records, then
+// turned into area, radius and centroid.
 __global__ void shadow_accum_kernel(StateView v, int64_t first, const ImageDev *imgs, int n_images, int64_t total,
                                     gray_shadow_info *out)
 {
@@ -1128,8 +1174,8 @@ __global__ void shadow_accum_kernel(StateView v, int64_t first, const ImageDev *
     gray_shadow_info *o = out + lo;
     if (st == GRAY_RAY_CAPTURED) {
         atomicAdd((unsigned long long *)&o->n_captured, 1ull);
-        atomicAdd(&o->alpha_c, im.a0 + ((double)col + 0.5) * im.da);
-        atomicAdd(&o->beta_c, im.b0 + ((double)row + 0.5) * im.db);
+        atomicAdd((unsigned long long *)&o->alpha_c, (unsigned long long)col);
+        atomicAdd((unsigned long long *)&o->beta_c, (unsigned long long)row);
     } else if (st == GRAY_RAY_ESCAPED) {
         atomicAdd((unsigned long long *)&o->n_escaped, 1ull);
     } else {
@@ -1143,12 +1189,19 @@ __global__ void shadow_final_kernel(const ImageDev *imgs, int n_images, gray_sha
     if (k >= n_images)
         return;
     gray_shadow_info s = out[k];
-    const double cell = fabs(imgs[k].da * imgs[k].db);
+    const ImageDev im = imgs[k];
+    const double cell = fabs(im.da * im.db);
+    const double sum_col = (double)*(const unsigned long long *)&out[k].alpha_c;
+    const double sum_row = (double)*(const unsigned long long *)&out[k].beta_c;
     s.area = (double)s.n_captured * cell;
     s.radius = sqrt(s.area / 3.14159265358979323846);
     if (s.n_captured > 0) {
-        s.alpha_c /= (double)s.n_captured;
-        s.beta_c /= (double)s.n_captured;
+        const double nc = (double)s.n_captured;
+        s.alpha_c = im.a0 + (sum_col / nc + 0.5) * im.da;
+        s.beta_c = im.b0 + (sum_row / nc + 0.5) * im.db;
+    } else {
+        s.alpha_c = 0.0;
+        s.beta_c = 0.0;
     }
     out[k] = s;
 }
@@ -1369,11 +1422,15 @@ int gray_create(gray_ctx **ctx, const gray_options *opt)
         delete c;
         return GRAY_ENOMEM;
     }
-    if (cudaMalloc((void **)&c->aux, AUX_WORDS * sizeof(unsigned long long)) != cudaSuccess) {
+    if (cudaMalloc((void **)&c->aux, AUX_ALLOC * sizeof(unsigned long long)) != cudaSuccess) {
         cudaFree(c->ws);
         cudaFreeHost(c->ws_host);
         delete c;
         return GRAY_ENOMEM;
+    }
+    if (cudaMemset(c->aux, 0, AUX_ALLOC * sizeof(unsigned long long)) != cudaSuccess) {
+        gray_destroy(c);
+        return GRAY_ECUDA;
     }
     std::memset(c->ws_host, 0, sizeof(Workspace));
     *ctx = c;
@@ -1454,8 +1511,7 @@ TraceArgs make_trace_args(gray_ctx *ctx, void *state, int64_t n_state, int64_t s
     A.max_steps = o.max_steps;
     A.refill = o.refill > 0 ? o.refill : 16;
     A.step_rule = o.step_rule;
-    ctx->epoch = ctx->epoch == 0x7fffffff ? 1 : ctx->epoch + 1;
-    A.epoch = ctx->epoch;
+    A.epoch_dev = (const int *)&ctx->aux[AUX_EPOCH];
     A.h_frac = o.h_frac;
     A.h_min = o.h_min;
     A.eps_xi = o.eps_xi;
@@ -1541,6 +1597,9 @@ int gray_trace(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, 
     cudaStream_t s = (cudaStream_t)stream;
     if (cudaMemsetAsync(ctx->ws, 0, sizeof(Workspace), s) != cudaSuccess)
         return GRAY_ECUDA;
+    bump_epoch_kernel<<<1, 1, 0, s>>>(ctx->aux);
+    if ((rc = check_launch()))
+        return rc;
     TraceArgs A = make_trace_args(ctx, state, n_state, step_budget);
     if (order) {
         A.order = order;
@@ -1615,6 +1674,9 @@ int gray_plan(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, c
                                                           ctx->aux);
     if ((rc = check_launch()))
         return rc;
+    bump_epoch_kernel<<<1, 1, 0, s>>>(ctx->aux);
+    if ((rc = check_launch()))
+        return rc;
     TraceArgs A = make_trace_args(ctx, state, n_state, probe_budget);
     A.order = order;
     A.n_queue_dev = &ctx->aux[AUX_PROBES];
@@ -1640,6 +1702,54 @@ int gray_plan(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, c
     if (rc)
         return rc;
     return cuda_err(e);
+}
+
+int gray_clear(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, int64_t first_ray, int64_t n,
+               void *stream)
+{
+    int rc = check_state(ctx, state, state_bytes, n_state);
+    if (rc)
+        return rc;
+    if (n < 0 || first_ray < 0 || first_ray + n > n_state)
+        return GRAY_EINVAL;
+    if (n == 0)
+        return GRAY_OK;
+    StateView v = make_view(state, n_state, ctx->opt.precision);
+    clear_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(v, first_ray, n);
+    return check_launch();
+}
+
+int gray_count_active(gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_state, const int64_t *ranges,
+                      int32_t n_ranges, int64_t *counts, void *stream)
+{
+    int rc = check_state(ctx, state, state_bytes, n_state);
+    if (rc)
+        return rc;
+    if (n_ranges < 0 || (n_ranges > 0 && (!ranges || !counts)))
+        return GRAY_EINVAL;
+    for (int k = 0; k < n_ranges; ++k)
+        if (ranges[2 * k] < 0 || ranges[2 * k + 1] < 0 || ranges[2 * k] + ranges[2 * k + 1] > n_state)
+            return GRAY_EINVAL;
+    if (n_ranges == 0)
+        return GRAY_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *dr = nullptr, *dc = nullptr;
+    if ((rc = upload_table(ranges, 2 * sizeof(int64_t) * (size_t)n_ranges, s, &dr)))
+        return rc;
+    if (cudaMallocAsync(&dc, sizeof(unsigned long long) * (size_t)n_ranges, s) != cudaSuccess) {
+        cudaFreeAsync(dr, s);
+        return GRAY_ECUDA;
+    }
+    StateView v = make_view((void *)state, n_state, ctx->opt.precision);
+    count_ranges_kernel<<<(unsigned)n_ranges, 256, 0, s>>>(v.S0, (const long long *)dr, (unsigned long long *)dc);
+    rc = check_launch();
+    if (!rc && cudaMemcpyAsync(counts, dc, sizeof(int64_t) * (size_t)n_ranges, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        rc = GRAY_ECUDA;
+    cudaFreeAsync(dr, s);
+    cudaFreeAsync(dc, s);
+    if (!rc && cudaStreamSynchronize(s) != cudaSuccess)
+        rc = GRAY_ECUDA;
+    return rc;
 }
 
 int gray_render(gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_state, int64_t first_ray, int64_t n,

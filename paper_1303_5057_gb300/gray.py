@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "gray.h")
 
 # constants mirrored from include/gray.h (checked against it by the tests)
 OK, EINVAL, ECUDA, ENOMEM = 0, -1, -2, -3
-ACTIVE, CAPTURED, ESCAPED, STEP_CAP, NONFINITE = 0, 1, 2, 3, 4
+ACTIVE, CAPTURED, ESCAPED, STEP_CAP, NONFINITE, EMPTY = 0, 1, 2, 3, 4, 5
 FP64, FP32, FP32_KAHAN, FP32_KAHAN_SEL64 = 0, 1, 2, 3
 STEP_BENCH, STEP_EQ2 = 0, 1
 RENDER_PIXELS64, RENDER_PIXELS32, RENDER_RECORD, RENDER_INVARIANTS = 0, 1, 3, 4
@@ -112,6 +112,10 @@ def lib():
     L.gray_plan.argtypes = [vp, vp, sz, i64, C.POINTER(_Image), i32, i64, i32, i32, vp, sz, vp]
     L.gray_plan.restype = C.c_int
     L.gray_trace.restype = C.c_int
+    L.gray_clear.argtypes = [vp, vp, sz, i64, i64, i64, vp]
+    L.gray_clear.restype = C.c_int
+    L.gray_count_active.argtypes = [vp, vp, sz, i64, C.POINTER(i64), i32, C.POINTER(i64), vp]
+    L.gray_count_active.restype = C.c_int
     L.gray_render.argtypes = [vp, vp, sz, i64, i64, i64, i32, vp, sz, vp]
     L.gray_render.restype = C.c_int
     L.gray_shadow.argtypes = [vp, vp, sz, i64, i64, C.POINTER(_Image), i32, vp, sz, vp]
@@ -245,6 +249,23 @@ def gray_plan(ctx, state, n_state, images, first_ray=0, probe_stride=4, probe_bu
                            int(first_ray), int(probe_stride), int(probe_budget), _ptr(order),
                            order.numel() * order.element_size(), _stream(stream)), "gray_plan")
     return order[:total]
+
+
+def gray_clear(ctx, state, n_state, first_ray, n, stream=None):
+    return _check(lib().gray_clear(ctx, _ptr(state), state.numel() * state.element_size(), int(n_state),
+                                   int(first_ray), int(n), _stream(stream)), "gray_clear")
+
+
+def gray_count_active(ctx, state, n_state, ranges, stream=None):
+    """ranges: list of (first_ray, count).  Returns a list of active counts."""
+    k = len(ranges)
+    arr = (C.c_int64 * max(1, 2 * k))()
+    for j, (f, c) in enumerate(ranges):
+        arr[2 * j], arr[2 * j + 1] = int(f), int(c)
+    out = (C.c_int64 * max(1, k))()
+    _check(lib().gray_count_active(ctx, _ptr(state), state.numel() * state.element_size(), int(n_state), arr, k, out,
+                                   _stream(stream)), "gray_count_active")
+    return [int(out[j]) for j in range(k)]
 
 
 _PER = {RENDER_PIXELS64: 32, RENDER_PIXELS32: 16, RENDER_RECORD: 17 * 8, RENDER_INVARIANTS: 4 * 8}

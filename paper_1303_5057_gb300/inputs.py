@@ -139,20 +139,23 @@ def mixed_rays(n: int = 1 << 26, seed_index: int = 2, offset: int = 0):
     near = (np.arange(offset, offset + n) % 2) == 1
     sgn = np.where(uniform(s + 55, n, offset=offset) < 0.5, -1.0, 1.0)
     off = uniform(s + 66, n, -0.1, 0.1, offset)
-    todo = near.copy()
+    todo = np.nonzero(near)[0]
     for attempt in range(8):
-        if not todo.any():
+        if todo.size == 0:
             break
-        u = uniform(s + 44 + 1000 * attempt, n, 0.02, 0.98, offset)
-        pa, pb, ok = _bardeen_point(a, inc, u)
-        qa, qb, ok2 = _bardeen_point(a, inc, np.minimum(u + 1e-4, 1.0))
-        take = todo & ok & ok2
-        ta, tb = qa - pa, sgn * (qb - pb)
+        u = uniform(s + 44 + 1000 * attempt, n, 0.02, 0.98, offset)[todo]
+        at, it = a[todo], inc[todo]
+        pa, pb, ok = _bardeen_point(at, it, u)
+        qa, qb, ok2 = _bardeen_point(at, it, np.minimum(u + 1e-4, 1.0))
+        take = ok & ok2
+        sg = sgn[todo]
+        ta, tb = qa - pa, sg * (qb - pb)
         nrm = np.hypot(ta, tb)
         nrm = np.where(nrm > 0, nrm, 1.0)
-        al = np.where(take, pa + off * (tb / nrm), al)
-        be = np.where(take, sgn * pb - off * (ta / nrm), be)
-        todo &= ~take
+        idx = todo[take]
+        al[idx] = (pa + off[todo] * (tb / nrm))[take]
+        be[idx] = (sg * pb - off[todo] * (ta / nrm))[take]
+        todo = todo[~take]
     rays = np.empty((n, 5))
     rays[:, 0] = al
     rays[:, 1] = be
