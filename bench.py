@@ -42,6 +42,11 @@ SPECIAL_PER_STEP = {"sincos": 5, "div": 15}
 # FP32 non-tensor peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz.
 SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0
+# DRAM bytes (read + write) of one launch of the dominant kernel (the
+# single-precision pass of this workload) from an ncu capture, see
+# profiles/trace32_kernel_kerr1024_sel64_planned.md: 140,282,624 read +
+# 58,024,448 written.
+TRAFFIC_BYTES = 198307072
 # FP64 non-tensor: 2 FP64 lanes per SM on this part.
 FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1000.0
 
@@ -354,6 +359,7 @@ def main():
     opt = gray.Options(precision=prec, max_steps=10000, r_sw=args.r_sw, step_rule=rule, block=args.block,
                        blocks_per_sm=args.blocks_per_sm, refill=args.refill)
     tr = gray.Tracer(opt, n)
+    gray.gray_set_timing(tr.ctx, True)
     stream = torch.cuda.current_stream()
     out_dev = torch.empty(16 * n, dtype=torch.uint8, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
@@ -376,16 +382,16 @@ def main():
     for _ in range(max(args.warmup, 1)):
         one_step()
     tr.setup([im])
-    if args.no_plan:
-        _, _, stats = tr.trace()
-        steps_per_pass, fp64_steps = stats[0], stats[2]
-    else:
-        # the probe steps are counted by a stats read after the plan
+    if not args.no_plan:
         order = tr.plan([im], probe_stride=args.probe_stride, probe_budget=args.probe_budget, order=order_buf)
         _, _, stats = tr.trace(order=order)
-        rec = tr.records()
-        steps_per_pass = int(rec[:, 1].sum())
-        fp64_steps = int(rec[:, 16].sum())
+    else:
+        _, _, stats = tr.trace()
+    _, _, _, zone_steps = gray.gray_timings(tr.ctx)
+    main_pass_steps = stats[0] - zone_steps  # steps of the dominant kernel (single-precision pass)
+    rec = tr.records()
+    steps_per_pass = int(rec[:, 1].sum())  # every step of the hot path, probe steps included
+    fp64_steps = int(rec[:, 16].sum())
     torch.cuda.synchronize()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
@@ -397,6 +403,7 @@ def main():
     sampler.start()
     time.sleep(0.3)
     launches0 = gray.gray_launch_count()
+    pass_ms = []
     for k in range(args.steps):
         flush.zero_()  # L2 flush between timed steps (outside the events)
         e0, e1, e2, e3 = ev[k]
@@ -407,6 +414,7 @@ def main():
         e2.record(stream)
         tr.render(gray.RENDER_PIXELS32, out=out_dev)
         e3.record(stream)
+        pass_ms.append(gray.gray_timings(tr.ctx)[:3])  # events of this step's passes (waits for them)
     torch.cuda.synchronize()
     launches = gray.gray_launch_count() - launches0
     clocks = sampler.stop()
@@ -418,8 +426,10 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     value = world * steps_per_pass * args.steps / (total_ms / 1000.0)
-    trace_avg_s = statistics.mean(trace_ms) / 1000.0
-    achieved = F_STEP * steps_per_pass / trace_avg_s / 1e12
+    main_ms = statistics.mean(p[0] for p in pass_ms)
+    zone_ms = statistics.mean(p[1] for p in pass_ms) if pass_ms[0][1] >= 0 else None
+    probe_ms = statistics.mean(p[2] for p in pass_ms) if pass_ms[0][2] >= 0 and not args.no_plan else None
+    achieved = F_STEP * main_pass_steps / (main_ms / 1000.0) / 1e12
 
     # ---- end to end through the C ABI: host image table in, pixels out to pinned host ----
     host_out = torch.empty(16 * n, dtype=torch.uint8, pin_memory=True)
@@ -475,9 +485,13 @@ def main():
             "steps_per_pass": steps_per_pass, "fp64_steps_per_pass": fp64_steps,
             "trace_ms": statistics.mean(trace_ms),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES,
+                         "kernel": "trace32_kernel (single-precision pass)", "kernel_ms": main_ms,
+                         "kernel_steps": main_pass_steps,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (FP32 non-tensor, max clock)",
                          "flop_per_step": F_STEP, "special_per_step": SPECIAL_PER_STEP},
+            "passes_ms": {"single": main_ms, "zone": zone_ms, "probe": probe_ms,
+                          "zone_steps": zone_steps, "setup_plan_trace_render": total_ms / args.steps},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 72, "d2h_bytes_per_step": 16 * n},
             "gpu_launches": launches,

@@ -288,6 +288,19 @@ int gray_setup_noalloc(int32_t precision, const gray_image *images_host, int32_t
 int gray_eval(int32_t what, int32_t precision, const double *in_dev, int64_t n,
               double *out_dev, void *stream);
 
+/* Record CUDA events around the passes of every later gray_trace and
+ * gray_plan call of this context (on = 1) or stop (on = 0).  Diagnostic.
+ * Errors: GRAY_EINVAL (NULL context), GRAY_ECUDA (event creation). */
+int gray_set_timing(gray_ctx *ctx, int32_t on);
+
+/* Durations of the last call's passes, in milliseconds (-1 where the pass did
+ * not run or timing is off): ms_host[0] the single-precision (or FP64) pass
+ * of gray_trace, ms_host[1] its zone pass (GRAY_FP32_KAHAN_SEL64), ms_host[2]
+ * the probe pass of gray_plan.  If zone_steps_host is not NULL it receives
+ * the steps the zone pass took in the last gray_trace.  Waits for the events.
+ * Errors: GRAY_EINVAL, GRAY_ECUDA. */
+int gray_timings(gray_ctx *ctx, double *ms_host, int64_t *zone_steps_host);
+
 /* Human-readable text of a return code; never NULL. */
 const char *gray_strerror(int code);
 

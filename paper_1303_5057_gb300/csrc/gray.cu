@@ -155,7 +155,7 @@ struct Workspace {
     unsigned long long active;  // rays left active by this call
     unsigned long long handoff; // rays appended to the hand-off list in this round
     unsigned long long demoted; // rays returned to single precision in this round
-    unsigned long long pad;
+    unsigned long long zone_steps; // steps taken by the zone kernel in this call
 };
 
 } // namespace
@@ -167,6 +167,9 @@ struct gray_ctx {
     int device = 0;
     int num_sms = 0;
     unsigned long long *aux = nullptr; // device: planning counters, histograms, call epoch
+    bool timing = false;               // record events around the passes of each call
+    cudaEvent_t ev[6] = {};            // [0,1] single pass, [2,3] zone pass, [4,5] plan probe pass
+    bool ev_used[3] = {false, false, false};
 };
 
 namespace {
@@ -324,15 +327,15 @@ __device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, 
     const T kt2 = fma(hh, a1[0], y[4]), kr2 = fma(hh, a1[1], y[5]), kh2 = fma(hh, a1[2], y[6]),
             kp2 = fma(hh, a1[3], y[7]);
     const T dr = KAHAN ? -c[1] : T(0), dth = KAHAN ? -c[2] : T(0);
-    accel_geo(H, geometry(H, r2, th2, dr, dth), kt2, kr2, kh2, kp2, a2);
+    accel_geo(H, geometry_rel(H, g, r2, hh * y[6], th2, dr, dth), kt2, kr2, kh2, kp2, a2);
     const T r3 = fma(hh, kr2, y[1]), th3 = fma(hh, kh2, y[2]);
     const T kt3 = fma(hh, a2[0], y[4]), kr3 = fma(hh, a2[1], y[5]), kh3 = fma(hh, a2[2], y[6]),
             kp3 = fma(hh, a2[3], y[7]);
-    accel_geo(H, geometry(H, r3, th3, dr, dth), kt3, kr3, kh3, kp3, a3);
+    accel_geo(H, geometry_rel(H, g, r3, hh * kh2, th3, dr, dth), kt3, kr3, kh3, kp3, a3);
     const T r4 = fma(h, kr3, y[1]), th4 = fma(h, kh3, y[2]);
     const T kt4 = fma(h, a3[0], y[4]), kr4 = fma(h, a3[1], y[5]), kh4 = fma(h, a3[2], y[6]),
             kp4 = fma(h, a3[3], y[7]);
-    accel_geo(H, geometry(H, r4, th4, dr, dth), kt4, kr4, kh4, kp4, a4);
+    accel_geo(H, geometry_rel(H, g, r4, h * kh3, th4, dr, dth), kt4, kr4, kh4, kp4, a4);
     const T h6 = sixth(h);
     T inc[8];
     inc[0] = h6 * (y[4] + T(2) * (kt2 + kt3) + kt4);
@@ -464,7 +467,8 @@ __device__ __forceinline__ unsigned long long warp_count(unsigned long long *ctr
 
 template <typename T>
 __device__ __forceinline__ void warp_stats(const TraceArgs &A, int lane, unsigned long long steps,
-                                           unsigned long long euler, unsigned long long fp64)
+                                           unsigned long long euler, unsigned long long fp64,
+                                           bool zone = false)
 {
     const unsigned FULL = 0xffffffffu;
 #pragma unroll
@@ -476,6 +480,8 @@ __device__ __forceinline__ void warp_stats(const TraceArgs &A, int lane, unsigne
     if (lane == 0) {
         if (steps)
             atomicAdd(&A.ws->steps, steps);
+        if (steps && zone)
+            atomicAdd(&A.ws->zone_steps, steps);
         if (euler)
             atomicAdd(&A.ws->euler, euler);
         if (fp64)
@@ -887,7 +893,7 @@ __global__ void __launch_bounds__(128, 1) zone_kernel(TraceArgs A)
             has = false;
         }
     }
-    warp_stats<double>(A, lane, tot_steps, tot_euler, tot_fp64);
+    warp_stats<double>(A, lane, tot_steps, tot_euler, tot_fp64, true);
 }
 
 // Mark rays as empty slots (never traced, never counted as active).
@@ -1441,6 +1447,9 @@ void gray_destroy(gray_ctx *ctx)
 {
     if (!ctx)
         return;
+    for (int k = 0; k < 6; ++k)
+        if (ctx->ev[k])
+            cudaEventDestroy(ctx->ev[k]);
     cudaFree(ctx->ws);
     cudaFree(ctx->aux);
     cudaFreeHost(ctx->ws_host);
@@ -1606,18 +1615,34 @@ int gray_trace(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, 
         A.n_queue = n_order;
     }
     const int64_t work = order ? n_order : n_state;
+    ctx->ev_used[0] = ctx->ev_used[1] = false;
     if (n_state > 0 && work > 0) {
+        if (ctx->timing) {
+            cudaEventRecord(ctx->ev[0], s);
+            ctx->ev_used[0] = true;
+        }
         if ((rc = launch_pass(ctx, A, work, s)))
             return rc;
+        if (ctx->timing)
+            cudaEventRecord(ctx->ev[1], s);
         if (ctx->opt.precision == GRAY_FP32_KAHAN_SEL64) {
             // the zone kernel takes the rays the single pass handed off (the
             // count stays on the device)
             if (cudaMemsetAsync(&ctx->ws->head, 0, sizeof(unsigned long long), s) != cudaSuccess)
                 return GRAY_ECUDA;
             const int block = ctx->opt.block > 0 ? ctx->opt.block : 128;
-            zone_kernel<<<persistent_grid(ctx, (const void *)zone_kernel, block, work), block, 0, s>>>(A);
+            // rays spend only a few steps in the zone: refill lanes often
+            TraceArgs Z = A;
+            Z.refill = 2;
+            if (ctx->timing) {
+                cudaEventRecord(ctx->ev[2], s);
+                ctx->ev_used[1] = true;
+            }
+            zone_kernel<<<persistent_grid(ctx, (const void *)zone_kernel, block, work), block, 0, s>>>(Z);
             if ((rc = check_launch()))
                 return rc;
+            if (ctx->timing)
+                cudaEventRecord(ctx->ev[3], s);
         }
     }
     if (!n_active_host && !stats_host)
@@ -1680,12 +1705,19 @@ int gray_plan(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, c
     TraceArgs A = make_trace_args(ctx, state, n_state, probe_budget);
     A.order = order;
     A.n_queue_dev = &ctx->aux[AUX_PROBES];
+    ctx->ev_used[2] = false;
+    if (ctx->timing) {
+        cudaEventRecord(ctx->ev[4], s);
+        ctx->ev_used[2] = true;
+    }
     int64_t probes_max = 0;
     for (int k = 0; k < n_images; ++k)
         probes_max += (int64_t)((images[k].nx + probe_stride - 1) / probe_stride) *
                       ((images[k].ny + probe_stride - 1) / probe_stride);
     if ((rc = launch_pass(ctx, A, probes_max, s)))
         return rc;
+    if (ctx->timing)
+        cudaEventRecord(ctx->ev[5], s);
     // 3. predicted cost -> bucket histogram -> descending offsets -> queue
     const StateView v = make_view(state, n_state, ctx->opt.precision);
     plan_hist_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, probe_stride, probe_budget,
@@ -1702,6 +1734,40 @@ int gray_plan(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, c
     if (rc)
         return rc;
     return cuda_err(e);
+}
+
+int gray_set_timing(gray_ctx *ctx, int32_t on)
+{
+    if (!ctx)
+        return GRAY_EINVAL;
+    if (on && !ctx->ev[0])
+        for (int k = 0; k < 6; ++k)
+            if (cudaEventCreate(&ctx->ev[k]) != cudaSuccess)
+                return GRAY_ECUDA;
+    ctx->timing = on != 0;
+    return GRAY_OK;
+}
+
+int gray_timings(gray_ctx *ctx, double *ms_host, int64_t *zone_steps_host)
+{
+    if (!ctx || !ms_host)
+        return GRAY_EINVAL;
+    for (int k = 0; k < 3; ++k) {
+        ms_host[k] = -1.0;
+        if (!ctx->timing || !ctx->ev_used[k])
+            continue;
+        float ms = 0.0f;
+        if (cudaEventSynchronize(ctx->ev[2 * k + 1]) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, ctx->ev[2 * k], ctx->ev[2 * k + 1]) != cudaSuccess)
+            return GRAY_ECUDA;
+        ms_host[k] = ms;
+    }
+    if (zone_steps_host) {
+        if (cudaMemcpy(ctx->ws_host, ctx->ws, sizeof(Workspace), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return GRAY_ECUDA;
+        *zone_steps_host = (int64_t)ctx->ws_host->zone_steps;
+    }
+    return GRAY_OK;
 }
 
 int gray_clear(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, int64_t first_ray, int64_t n,

@@ -251,6 +251,16 @@ template <typename T> struct Geo {
     T r, s, c, Sigma, Delta, iS, iD, is;
 };
 
+// 1/Sigma, 1/Delta and 1/sin from one reciprocal of Sigma Delta sin.
+template <typename T> __device__ __forceinline__ void geometry_reciprocals(Geo<T> &g)
+{
+    const T Ds = g.Delta * g.s, SD = g.Sigma * g.Delta;
+    const T inv = recip(SD * g.s);
+    g.iS = inv * Ds;
+    g.iD = inv * (g.Sigma * g.s);
+    g.is = inv * SD;
+}
+
 // dr and dth are the low words of a compensated single-precision point (the
 // true point is (r + dr, th + dth)): sin and cos get their first-order
 // correction and Delta is formed from the compensated r and the split r_+, so
@@ -273,17 +283,67 @@ __device__ __forceinline__ Geo<T> geometry(const Hole<T> &H, T r, T th, T dr = T
         g.Delta = fma(r - H.rp, r - H.rm, H.dc);
     }
     g.Sigma = fma(H.a * H.a, g.c * g.c, r * r);
-    if (sizeof(T) == 4) {
-        const T Ds = g.Delta * g.s, SD = g.Sigma * g.Delta;
-        const T inv = recip(SD * g.s);
-        g.iS = inv * Ds;
-        g.iD = inv * (g.Sigma * g.s);
-        g.is = inv * SD;
-    } else {
-        g.iS = T(1) / g.Sigma;
-        g.iD = T(1) / g.Delta;
-        g.is = T(1) / g.s;
-    }
+    geometry_reciprocals(g);
+    return g;
+}
+
+// sin and cos of a small angle d by their Taylor series: |d| <= 0.25,
+// truncation below 1e-11 (single, degrees 7 and 8) and 3e-18 (double,
+// degrees 11 and 12).  Returns false for larger |d|.
+__device__ __forceinline__ bool small_sincos(float d, float *s, float *c)
+{
+    if (!(fabsf(d) <= 0.25f))
+        return false;
+    const float d2 = d * d;
+    float ps = fmaf(d2, -1.98412698e-04f, 8.33333333e-03f);
+    ps = fmaf(ps, d2, -1.66666667e-01f);
+    *s = fmaf(ps * d2, d, d);
+    float pc = fmaf(d2, 2.48015873e-05f, -1.38888889e-03f);
+    pc = fmaf(pc, d2, 4.16666667e-02f);
+    pc = fmaf(pc, d2, -0.5f);
+    *c = fmaf(pc, d2, 1.0f);
+    return true;
+}
+__device__ __forceinline__ bool small_sincos(double d, double *s, double *c)
+{
+    if (!(fabs(d) <= 0.25))
+        return false;
+    const double d2 = d * d;
+    double ps = fma(d2, -2.505210838544172e-08, 2.7557319223985893e-06);
+    ps = fma(ps, d2, -1.984126984126984e-04);
+    ps = fma(ps, d2, 8.333333333333333e-03);
+    ps = fma(ps, d2, -1.6666666666666666e-01);
+    *s = fma(ps * d2, d, d);
+    double pc = fma(d2, 2.08767569878681e-09, -2.755731922398589e-07);
+    pc = fma(pc, d2, 2.48015873015873e-05);
+    pc = fma(pc, d2, -1.388888888888889e-03);
+    pc = fma(pc, d2, 4.1666666666666664e-02);
+    pc = fma(pc, d2, -0.5);
+    *c = fma(pc, d2, 1.0);
+    return true;
+}
+
+// Geometry of an RK4 stage point whose polar angle is the step's start angle
+// plus d: sin and cos come from the start point's by the angle-addition
+// formulas (the start point's values already carry the compensation), which
+// costs two short series instead of a full sin/cos; far stages (|d| > 0.25)
+// take the full evaluation at th with its low word dth.
+template <typename T>
+__device__ __forceinline__ Geo<T> geometry_rel(const Hole<T> &H, const Geo<T> &g0, T r, T d, T th, T dr, T dth)
+{
+    T sd, cd;
+    if (!small_sincos(d, &sd, &cd))
+        return geometry(H, r, th, dr, dth);
+    Geo<T> g;
+    g.r = r;
+    g.s = fma(g0.s, cd, g0.c * sd);
+    g.c = fma(g0.c, cd, -(g0.s * sd));
+    if (sizeof(T) == 4)
+        g.Delta = fma((r - H.rp) + (dr - H.rp_lo), (r - H.rm) + dr, H.dc);
+    else
+        g.Delta = fma(r - H.rp, r - H.rm, H.dc);
+    g.Sigma = fma(H.a * H.a, g.c * g.c, r * r);
+    geometry_reciprocals(g);
     return g;
 }
 

@@ -122,6 +122,10 @@ def lib():
     L.gray_shadow.restype = C.c_int
     L.gray_eval.argtypes = [i32, i32, vp, i64, vp, vp]
     L.gray_eval.restype = C.c_int
+    L.gray_set_timing.argtypes = [vp, i32]
+    L.gray_set_timing.restype = C.c_int
+    L.gray_timings.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64)]
+    L.gray_timings.restype = C.c_int
     L.gray_strerror.argtypes = [C.c_int]
     L.gray_strerror.restype = C.c_char_p
     L.gray_launch_count.argtypes = []
@@ -249,6 +253,18 @@ def gray_plan(ctx, state, n_state, images, first_ray=0, probe_stride=4, probe_bu
                            int(first_ray), int(probe_stride), int(probe_budget), _ptr(order),
                            order.numel() * order.element_size(), _stream(stream)), "gray_plan")
     return order[:total]
+
+
+def gray_set_timing(ctx, on=True):
+    return _check(lib().gray_set_timing(ctx, 1 if on else 0), "gray_set_timing")
+
+
+def gray_timings(ctx):
+    """(single pass ms, zone pass ms, probe pass ms, zone steps) of the last calls."""
+    ms = (C.c_double * 3)()
+    zs = C.c_int64()
+    _check(lib().gray_timings(ctx, ms, C.byref(zs)), "gray_timings")
+    return float(ms[0]), float(ms[1]), float(ms[2]), int(zs.value)
 
 
 def gray_clear(ctx, state, n_state, first_ray, n, stream=None):
