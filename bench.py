@@ -71,7 +71,7 @@ def parse_args():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-rays", type=int, default=16384)
     p.add_argument("--workload", default="kerr1024",
-                   choices=["kerr1024", "schwarzschild64", "mixed", "sweep", "serve"])
+                   choices=["kerr1024", "schwarzschild64", "mixed", "sweep", "serve", "projection"])
     p.add_argument("--rays", type=int, default=1 << 22, help="mixed workload: rays")
     p.add_argument("--images", type=int, default=256, help="sweep workload: images")
     p.add_argument("--rates", default="10,30,100,300,1000", help="serve workload: req/s")
@@ -316,6 +316,41 @@ def run_serve(args):
     return 0
 
 
+def run_projection(args):
+    """Sec. 3 grid projection (a = 0.95, i = 60 deg, r = 1000 M, each ray stops
+    on the equatorial plane): time per image against the number of geodesics,
+    in FP64 (as the paper's Fig. 4) and in compensated FP32 with the double
+    zone; the oracle on the host cores for the smaller images."""
+    import torch
+    import oracle
+    from paper_1303_5057_gb300 import gray
+    from paper_1303_5057_gb300 import inputs as I
+    rows = []
+    for side in (8, 16, 32, 64, 128, 256, 512, 1024):
+        im = I.Image(a=0.95, incl=math.radians(60.0), nx=side, ny=side, alpha0=-15, alpha1=15, beta0=-15, beta1=15)
+        row = {"geodesics": im.n}
+        for name, prec in (("gpu_fp64", gray.FP64), ("gpu_fp32_kahan_sel64", gray.FP32_KAHAN_SEL64)):
+            tr = gray.Tracer(gray.Options(precision=prec, max_steps=20000, r_sw=args.r_sw, stop_equator=1), im.n)
+            out = torch.empty(16 * im.n, dtype=torch.uint8, device="cuda")
+
+            def step():
+                tr.setup([im])
+                tr.trace(wait=False)
+                tr.render(gray.RENDER_PIXELS32, out=out)
+            step()
+            ms, _ = _timed(step, 3)
+            tr.close()
+            row[name + "_ms"] = ms
+        if im.n <= 16384:
+            rays = oracle.image_rays(im.a, im.incl, im.r_obs, im.nx, im.ny, im.alpha0, im.alpha1, im.beta0, im.beta1)
+            t0 = time.perf_counter()
+            oracle.trace_many(rays, oracle.Options(max_steps=20000, stop_equator=1), nthreads=1)
+            row["cpu_oracle_1core_ms"] = 1000.0 * (time.perf_counter() - t0)
+        rows.append(row)
+        print(json.dumps({"workload": "grid_projection_a0.95_i60", **row}), flush=True)
+    return 0
+
+
 # --------------------------------------------------------------- GPU arm ---
 
 def main():
@@ -329,7 +364,7 @@ def main():
         build.build()
         gray.lib()
         return {"schwarzschild64": run_schwarzschild64, "mixed": run_mixed, "sweep": run_sweep,
-                "serve": run_serve}[args.workload](args)
+                "serve": run_serve, "projection": run_projection}[args.workload](args)
 
     import torch
 

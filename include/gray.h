@@ -49,6 +49,7 @@ extern "C" {
 #define GRAY_RAY_STEP_CAP 3  /* hit max_steps */
 #define GRAY_RAY_NONFINITE 4 /* state became NaN or Inf */
 #define GRAY_RAY_EMPTY 5     /* an unused slot of a resident pool (gray_clear) */
+#define GRAY_RAY_EQUATOR 6   /* crossed the equatorial plane (stop_equator): final point on it */
 
 /* ---- arithmetic of the trace ---------------------------------------- */
 #define GRAY_FP64 0             /* every step in double precision */
@@ -100,6 +101,7 @@ typedef struct gray_options {
     int32_t blocks_per_sm; /* resident blocks per SM of the persistent grid, 0 = default */
     int32_t refill;        /* steps between warp refills from the work queue, 0 = default */
     int32_t launch;        /* GRAY_LAUNCH_PERSISTENT or GRAY_LAUNCH_ONE_PER_THREAD (single precision only) */
+    int32_t stop_equator;  /* 1: also stop at the first crossing of theta = pi/2 (the grid projection of Sec. 3) */
     double h_frac;         /* 1/32: the f of the benchmark rule, the Delta of Eq. 2 */
     double h_min;          /* 1e-3: floor on |h| */
     double cap_frac;       /* 1.01: capture when r <= cap_frac * r_h */

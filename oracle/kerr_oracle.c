@@ -54,7 +54,7 @@
 #define PH_ 3
 
 /* Status codes written per ray. */
-enum { ORC_ACTIVE = 0, ORC_CAPTURED = 1, ORC_ESCAPED = 2, ORC_STEP_CAP = 3, ORC_NONFINITE = 4 };
+enum { ORC_ACTIVE = 0, ORC_CAPTURED = 1, ORC_ESCAPED = 2, ORC_STEP_CAP = 3, ORC_NONFINITE = 4, ORC_EQUATOR = 6 };
 
 /* Step rules: the benchmark rule (default) and the paper's full Eq. 2. */
 enum { ORC_STEP_BENCH = 0, ORC_STEP_EQ2 = 1 };
@@ -68,6 +68,7 @@ typedef struct {
     double r_esc_frac; /* escape radius as a multiple of r_obs (reading: 1) */
     int32_t max_steps; /* hard step cap per ray */
     int32_t step_rule; /* ORC_STEP_BENCH or ORC_STEP_EQ2 */
+    int32_t stop_equator; /* 1: also stop at the first crossing of theta = pi/2 (Sec. 3 projection) */
 } orc_options;
 
 /* ------------------------------------------------------------------ */
@@ -369,6 +370,30 @@ void orc_stop_surface(const double y0[8], const double y1[8], double h, double r
         fin[m] = p[m];
 }
 
+/* Grid projection (Sec. 3): the point where the ray first crosses the
+ * equatorial plane theta = pi/2 within the step (y0, y1): 60 bisections of
+ * the Hermite theta(s) - pi/2 on [0, 1], then Hermite for the other
+ * coordinates.  The pre-remap end state is used, so theta is continuous. */
+void orc_equator_crossing(const double y0[8], const double y1[8], double h, double fin[4])
+{
+    double lo = 0.0, hi = 1.0;
+    double f_lo = y0[TH_] - 0.5 * ORC_PI;
+    for (int it = 0; it < 60; ++it) {
+        double mid = 0.5 * (lo + hi);
+        double f_mid = orc_hermite(y0[TH_], y0[4 + TH_], y1[TH_], y1[4 + TH_], h, mid) - 0.5 * ORC_PI;
+        if ((f_mid > 0.0) == (f_lo > 0.0)) {
+            lo = mid;
+            f_lo = f_mid;
+        } else {
+            hi = mid;
+        }
+    }
+    double s = 0.5 * (lo + hi);
+    for (int m = 0; m < 4; ++m)
+        fin[m] = orc_hermite(y0[m], y0[4 + m], y1[m], y1[4 + m], h, s);
+    fin[TH_] = 0.5 * ORC_PI;
+}
+
 /* Per-ray result record (all doubles so that one flat array carries it):
  *  [0] status  [1] steps  [2] euler redos  [3] pole remaps
  *  [4..7] final (t, r, theta, phi) on the stop surface
@@ -414,7 +439,13 @@ int orc_trace(double M, double a, double r_obs, const orc_options *o, double y[8
             memcpy(fin, y1, 4 * sizeof(double));
             break;
         }
-        if (y1[R_] <= r_cap) {
+        if (o->stop_equator && (y[TH_] - 0.5 * ORC_PI) * (y1[TH_] - 0.5 * ORC_PI) < 0.0) {
+            /* reading: the crossing is tested before the horizon and escape
+             * stops, on the step's start state (theta in [0, pi]) and its
+             * pre-remap end state */
+            orc_equator_crossing(y, y1, h, fin);
+            status = ORC_EQUATOR;
+        } else if (y1[R_] <= r_cap) {
             orc_stop_surface(y, y1, h, r_cap, fin);
             status = ORC_CAPTURED;
         } else if (y1[R_] >= r_esc && h * y1[4 + R_] > 0.0) {

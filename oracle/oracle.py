@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-ACTIVE, CAPTURED, ESCAPED, STEP_CAP, NONFINITE = 0, 1, 2, 3, 4
+ACTIVE, CAPTURED, ESCAPED, STEP_CAP, NONFINITE, EQUATOR = 0, 1, 2, 3, 4, 6
 STEP_BENCH, STEP_EQ2 = 0, 1
 REC = 17  # doubles per ray record, see ``orc_trace``
 
@@ -27,7 +27,7 @@ class _Options(C.Structure):
     _fields_ = [("M", C.c_double), ("h_frac", C.c_double), ("h_min", C.c_double),
                 ("cap_frac", C.c_double), ("eps_xi", C.c_double),
                 ("r_esc_frac", C.c_double), ("max_steps", C.c_int32),
-                ("step_rule", C.c_int32)]
+                ("step_rule", C.c_int32), ("stop_equator", C.c_int32)]
 
 
 @dataclass
@@ -43,10 +43,12 @@ class Options:
     r_esc_frac: float = 1.0
     max_steps: int = 100000
     step_rule: int = STEP_BENCH
+    stop_equator: int = 0
 
     def _c(self):
         return _Options(self.M, self.h_frac, self.h_min, self.cap_frac, self.eps_xi,
-                        self.r_esc_frac, int(self.max_steps), int(self.step_rule))
+                        self.r_esc_frac, int(self.max_steps), int(self.step_rule),
+                        int(self.stop_equator))
 
 
 _lib = None
@@ -251,7 +253,7 @@ def image_rays(a, incl, r_obs, nx, ny, a0, a1, b0, b1):
 
 
 __all__ = [
-    "ACTIVE", "CAPTURED", "ESCAPED", "STEP_CAP", "NONFINITE", "STEP_BENCH", "STEP_EQ2",
+    "ACTIVE", "CAPTURED", "ESCAPED", "STEP_CAP", "NONFINITE", "EQUATOR", "STEP_BENCH", "STEP_EQ2",
     "REC", "Options", "horizon", "metric", "inverse_metric", "metric_derivs",
     "christoffel", "rhs", "null_norm", "xi", "invariants", "initial", "step_size",
     "rk4", "remap", "hermite", "stop_surface", "trace", "trace_many",

@@ -371,6 +371,9 @@ __device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, 
         status = GRAY_RAY_NONFINITE;
         for (int m = 0; m < 4; ++m)
             fin[m] = y1[m];
+    } else if (O.stop_equator && (y[2] - T(0.5) * pi_v<T>()) * (y1[2] - T(0.5) * pi_v<T>()) < T(0)) {
+        equator_crossing(y, y1, h, fin);
+        status = GRAY_RAY_EQUATOR;
     } else if (y1[1] <= H.r_cap) {
         stop_surface(y, y1, h, H.r_cap, fin);
         status = GRAY_RAY_CAPTURED;
@@ -423,6 +426,7 @@ struct TraceArgs {
     const int *epoch_dev; // call counter on the device (bumped by every gray_trace / gray_plan):
                           // S1.y == epoch means S1.z counts this call's steps
     int one_per_thread; // the paper's launch: thread g takes queue slot g only
+    int stop_equator;   // Sec. 3 grid projection: stop at the equatorial plane
     double h_frac, h_min, eps_xi, cap_frac, r_esc_frac, r_sw;
     Workspace *ws;
 };
@@ -502,6 +506,7 @@ template <int MODE> __global__ void __maxnreg__(96) trace32_kernel(TraceArgs A)
     O.h_min = (float)A.h_min;
     O.eps_xi = (float)A.eps_xi;
     O.step_rule = A.step_rule;
+    O.stop_equator = A.stop_equator;
 
     bool has = false, exhausted = false;
     int64_t id = 0;
@@ -639,6 +644,7 @@ __global__ void __launch_bounds__(128) trace64_kernel(TraceArgs A)
     O.h_min = A.h_min;
     O.eps_xi = A.eps_xi;
     O.step_rule = A.step_rule;
+    O.stop_equator = A.stop_equator;
 
     bool has = false, exhausted = false;
     int64_t id = 0;
@@ -742,11 +748,13 @@ __global__ void __launch_bounds__(128, 1) zone_kernel(TraceArgs A)
     Od.h_min = A.h_min;
     Od.eps_xi = A.eps_xi;
     Od.step_rule = A.step_rule;
+    Od.stop_equator = A.stop_equator;
     StepOpt<float> Of;
     Of.h_frac = (float)A.h_frac;
     Of.h_min = (float)A.h_min;
     Of.eps_xi = (float)A.eps_xi;
     Of.step_rule = A.step_rule;
+    Of.stop_equator = A.stop_equator;
     const int64_t n = (int64_t)*(volatile unsigned long long *)&A.ws->handoff;
     const int epoch = *A.epoch_dev;
 
@@ -1297,6 +1305,8 @@ int validate_options(const gray_options *o)
         return GRAY_EINVAL;
     if (o->launch != GRAY_LAUNCH_PERSISTENT && o->launch != GRAY_LAUNCH_ONE_PER_THREAD)
         return GRAY_EINVAL;
+    if (o->stop_equator != 0 && o->stop_equator != 1)
+        return GRAY_EINVAL;
     if (!finite_all({o->h_frac, o->h_min, o->cap_frac, o->eps_xi, o->r_esc_frac, o->r_sw}))
         return GRAY_EINVAL;
     if (!(o->h_frac > 0) || !(o->h_min > 0) || !(o->cap_frac >= 1.0) || !(o->eps_xi > 0) ||
@@ -1529,6 +1539,7 @@ TraceArgs make_trace_args(gray_ctx *ctx, void *state, int64_t n_state, int64_t s
     A.r_sw = o.r_sw;
     A.ws = ctx->ws;
     A.one_per_thread = o.launch == GRAY_LAUNCH_ONE_PER_THREAD;
+    A.stop_equator = o.stop_equator;
     return A;
 }
 

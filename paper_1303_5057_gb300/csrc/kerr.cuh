@@ -63,7 +63,8 @@ template <typename T> struct Hole {
 // Integration options used inside a step.
 template <typename T> struct StepOpt {
     T h_frac, h_min, eps_xi;
-    int step_rule; // 0: benchmark rule, 1: Eq. 2
+    int step_rule;    // 0: benchmark rule, 1: Eq. 2
+    int stop_equator; // 1: stop at the first crossing of theta = pi/2 (Sec. 3 projection)
 };
 
 // Build the per-ray constants in double precision (one square root per ray).
@@ -458,18 +459,20 @@ template <typename T> struct BisectIters;
 template <> struct BisectIters<float> { static constexpr int value = 30; };
 template <> struct BisectIters<double> { static constexpr int value = 60; };
 
-// Crossing fraction of the stop surface within the last step.  Double:
-// bisection of the Hermite r(s) - r_stop (60 halvings, as the oracle).  Single:
-// Newton's method from the secant estimate, kept inside the bracket (a Newton
-// step that leaves it is replaced by a bisection step), 6 iterations.
-template <typename T> __device__ __forceinline__ T crossing_fraction(const T *y0, const T *y1, T h, T r_stop)
+// Fraction s of the last step at which coordinate m (1: r, 2: theta) of the
+// Hermite interpolant reaches `target`.  Double: bisection (60 halvings, as
+// the oracle).  Single: Newton's method from the secant estimate, kept inside
+// the bracket (a Newton step that leaves it is replaced by a bisection step),
+// 6 iterations.
+template <typename T>
+__device__ __forceinline__ T crossing_fraction(const T *y0, const T *y1, T h, T target, int m = 1)
 {
     T lo = T(0), hi = T(1);
-    T f_lo = y0[1] - r_stop;
+    T f_lo = y0[m] - target;
     if (sizeof(T) == 8) {
         for (int it = 0; it < BisectIters<T>::value; ++it) {
             T mid = T(0.5) * (lo + hi);
-            T f_mid = hermite(y0[1], y0[5], y1[1], y1[5], h, mid) - r_stop;
+            T f_mid = hermite(y0[m], y0[4 + m], y1[m], y1[4 + m], h, mid) - target;
             if ((f_mid > T(0)) == (f_lo > T(0))) {
                 lo = mid;
                 f_lo = f_mid;
@@ -479,14 +482,14 @@ template <typename T> __device__ __forceinline__ T crossing_fraction(const T *y0
         }
         return T(0.5) * (lo + hi);
     }
-    const T f_hi = y1[1] - r_stop;
+    const T f_hi = y1[m] - target;
     T s = f_lo / (f_lo - f_hi);
     if (!(s > T(0) && s < T(1)))
         s = T(0.5);
-    const T p0 = y0[1], m0 = h * y0[5], p1 = y1[1], m1 = h * y1[5];
+    const T p0 = y0[m], m0 = h * y0[4 + m], p1 = y1[m], m1 = h * y1[4 + m];
     for (int it = 0; it < 6; ++it) {
         const T s2 = s * s;
-        const T f = hermite(p0, y0[5], p1, y1[5], h, s) - r_stop;
+        const T f = hermite(p0, y0[4 + m], p1, y1[4 + m], h, s) - target;
         const T df = (T(6) * s2 - T(6) * s) * p0 + (T(3) * s2 - T(4) * s + T(1)) * m0 + (T(6) * s - T(6) * s2) * p1 +
                      (T(3) * s2 - T(2) * s) * m1;
         if ((f > T(0)) == (f_lo > T(0)))
@@ -499,6 +502,17 @@ template <typename T> __device__ __forceinline__ T crossing_fraction(const T *y0
         s = sn;
     }
     return s;
+}
+
+// Grid projection (Sec. 3): the point where the step first crosses the
+// equatorial plane theta = pi/2 (start state and pre-remap end state).
+template <typename T> __device__ inline void equator_crossing(const T *y0, const T *y1, T h, T *fin)
+{
+    const T half_pi = T(0.5) * pi_v<T>();
+    const T s = crossing_fraction(y0, y1, h, half_pi, 2);
+    for (int m = 0; m < 4; ++m)
+        fin[m] = hermite(y0[m], y0[4 + m], y1[m], y1[4 + m], h, s);
+    fin[2] = half_pi;
 }
 
 // Final (t, r, theta, phi) on the stop surface r = r_stop: the crossing

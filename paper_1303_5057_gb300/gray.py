@@ -21,7 +21,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "gray.h")
 
 # constants mirrored from include/gray.h (checked against it by the tests)
 OK, EINVAL, ECUDA, ENOMEM = 0, -1, -2, -3
-ACTIVE, CAPTURED, ESCAPED, STEP_CAP, NONFINITE, EMPTY = 0, 1, 2, 3, 4, 5
+ACTIVE, CAPTURED, ESCAPED, STEP_CAP, NONFINITE, EMPTY, EQUATOR = 0, 1, 2, 3, 4, 5, 6
 FP64, FP32, FP32_KAHAN, FP32_KAHAN_SEL64 = 0, 1, 2, 3
 STEP_BENCH, STEP_EQ2 = 0, 1
 RENDER_PIXELS64, RENDER_PIXELS32, RENDER_RECORD, RENDER_INVARIANTS = 0, 1, 3, 4
@@ -42,7 +42,7 @@ class GrayError(RuntimeError):
 class _Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("step_rule", C.c_int32), ("max_steps", C.c_int32),
                 ("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill", C.c_int32),
-                ("launch", C.c_int32),
+                ("launch", C.c_int32), ("stop_equator", C.c_int32),
                 ("h_frac", C.c_double), ("h_min", C.c_double), ("cap_frac", C.c_double),
                 ("eps_xi", C.c_double), ("r_esc_frac", C.c_double), ("r_sw", C.c_double)]
 
@@ -69,6 +69,7 @@ class Options:
     blocks_per_sm: int = 0
     refill: int = 0
     launch: int = LAUNCH_PERSISTENT
+    stop_equator: int = 0
     h_frac: float = 1.0 / 32.0
     h_min: float = 1e-3
     cap_frac: float = 1.01

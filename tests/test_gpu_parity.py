@@ -257,6 +257,33 @@ def test_kerr_eq2_fp32_selective_fp64():
     assert np.median(np.abs(rec[sel, 6] - ref[sel, 6])) < 1e-6
 
 
+@pytest.mark.parametrize("a,incl_deg", [(0.95, 60.0), (0.0, 0.0), (0.95, 0.0)])
+def test_grid_projection_matches_oracle(a, incl_deg):
+    """Sec. 3 grid projection: each pixel's ray stops where it first crosses
+    the equatorial plane; FP64 reproduces the oracle's status and crossing
+    point (r, phi) to 1e-9; compensated FP32 with the double zone to 1e-4."""
+    im = I.Image(a=a, incl=math.radians(incl_deg), nx=40, ny=36, alpha0=-12, alpha1=12, beta0=-12, beta1=12)
+    rays = oracle.image_rays(im.a, im.incl, im.r_obs, im.nx, im.ny, im.alpha0, im.alpha1, im.beta0, im.beta1)
+    ref = oracle.trace_many(rays, oracle.Options(max_steps=20000, stop_equator=1))
+    far = P.band_mask((rays[:, 0], rays[:, 1]), a, max(im.incl, 1e-3))
+    rec64, _, _, _ = trace_image(im, gray.Options(precision=gray.FP64, max_steps=20000, stop_equator=1))
+    assert np.mean(ref[:, 0] == oracle.EQUATOR) > 0.5
+    same = rec64[:, 0] == ref[:, 0]
+    assert same[far].all()
+    eq = same & (ref[:, 0] == oracle.EQUATOR)
+    assert np.abs(rec64[eq, 5] - ref[eq, 5]).max() <= 1e-9 * np.abs(ref[eq, 5]).max()
+    assert np.abs(P.wrap(rec64[eq, 7] - ref[eq, 7])).max() <= 1e-9
+    assert np.all(rec64[eq, 6] == np.float64(math.pi / 2))
+    rec32, _, _, _ = trace_image(im, gray.Options(precision=gray.FP32_KAHAN_SEL64, max_steps=20000, r_sw=0.02,
+                                                  stop_equator=1))
+    same32 = (rec32[:, 0] == ref[:, 0]) & far
+    assert same32.sum() >= 0.9999 * far.sum()
+    eq32 = same32 & (ref[:, 0] == oracle.EQUATOR)
+    rel = np.abs(rec32[eq32, 5] - ref[eq32, 5]) / ref[eq32, 5]
+    assert np.percentile(rel, 99) < 1e-4
+    assert np.percentile(np.abs(P.wrap(rec32[eq32, 7] - ref[eq32, 7])), 99) < 1e-4
+
+
 def test_trace_split_over_calls_equals_one_call():
     """Resumable tracing (the step-limited mode of Sec. 2): many calls with a
     small per-call budget give bit-identical records to one call."""

@@ -361,3 +361,31 @@ def test_pole_crossing_ray_from_the_paper(orc):
     assert rec[3] >= g["min_pole_crossings"]
     assert rec[2] >= 1  # the Euler fallback of Eq. 4 fired
     assert g["r0_sin_theta0"] < T.polar_shadow_radius(a)
+
+
+@pytest.mark.parametrize("b", [2.5, 4.0, 6.0, 9.0, 20.0])
+def test_equator_crossing_matches_schwarzschild_quadrature(orc, b):
+    """Grid projection (Sec. 3): seen face-on, a Schwarzschild photon's orbit
+    contains the axis, so it meets the equatorial plane where its swept
+    orbital angle reaches pi/2 - theta_0, or is captured first when it plunges
+    before sweeping that much.  The oracle's interpolated crossing radius
+    matches the exact quadrature (impact parameter from the ray's own
+    invariants, b^2 = Q + L_z^2) to RK4 truncation, falling ~16x when the step
+    halves."""
+    errs = []
+    for hf in (1 / 32, 1 / 64):
+        y0 = orc.initial(M, 0.0, 1000.0, 0.0, b, 0.0)
+        E, L, Q, _ = orc.invariants(M, 0.0, y0)
+        b_true = math.sqrt(Q + L * L) / E
+        rec = orc.trace(0.0, 1000.0, y0, orc.Options(h_frac=hf, stop_equator=1))
+        target = math.pi / 2 - y0[2]
+        r_cap = 1.01 * 2.0
+        if b_true < 3 * math.sqrt(3) and T.schwarzschild_swept_to(b_true, y0[1], r_cap) < target:
+            assert rec[0] == orc.CAPTURED
+            return
+        assert rec[0] == orc.EQUATOR
+        assert rec[6] == pytest.approx(math.pi / 2)
+        r_eq = T.schwarzschild_radius_at_angle(b_true, y0[1], target)
+        errs.append(abs(rec[5] - r_eq) / r_eq)
+    assert errs[0] < 2e-6, errs
+    assert errs[1] < errs[0] / 6 or errs[1] < 1e-9, errs

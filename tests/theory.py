@@ -257,3 +257,46 @@ def angle_diff(x, y):
     """x - y wrapped into (-pi, pi]."""
     d = (np.asarray(x) - np.asarray(y) + math.pi) % (2.0 * math.pi) - math.pi
     return d
+
+
+# ---------------------------------------------------------------------------
+# Schwarzschild orbit: radius at a given swept angle (M = 1)
+# ---------------------------------------------------------------------------
+
+def schwarzschild_radius_at_angle(b, r0, psi):
+    """Radius where a photon of impact parameter b, followed inward from r0,
+    has swept the orbital angle psi (on the inward leg, or past its turning
+    point on the outward leg).  d psi / d r = 1 / (r^2 sqrt(1/b^2 - (1 - 2/r)/r^2))."""
+    from scipy import optimize
+
+    def g(r):
+        return 1.0 / (r * r * math.sqrt(max(1.0 / (b * b) - (1.0 - 2.0 / r) / (r * r), 1e-300)))
+
+    bc = 3.0 * math.sqrt(3.0)
+    if b > bc:
+        # turning point: largest root of r^3 - b^2 r + 2 b^2 = 0
+        roots = np.roots([1.0, 0.0, -b * b, 2.0 * b * b])
+        rmin = float(roots[np.abs(roots.imag) < 1e-9].real.max())
+
+        def swept_in(r):  # from r0 down to r >= rmin; u-substitution near rmin
+            def f(u):
+                rr = rmin + u * u
+                return 2.0 * u * g(rr)
+            return integrate.quad(f, math.sqrt(r - rmin), math.sqrt(r0 - rmin), epsabs=1e-13, epsrel=1e-13,
+                                  limit=400)[0]
+        total_in = swept_in(rmin)
+        if psi <= total_in:
+            return optimize.brentq(lambda r: swept_in(r) - psi, rmin, r0, xtol=1e-13, rtol=1e-14)
+        return optimize.brentq(lambda r: total_in + (total_in - swept_in(r)) - psi, rmin, r0, xtol=1e-13,
+                               rtol=1e-14)
+
+    def swept(r):
+        return integrate.quad(g, r, r0, epsabs=1e-13, epsrel=1e-13, limit=400)[0]
+    return optimize.brentq(lambda r: swept(r) - psi, 2.0 + 1e-9, r0, xtol=1e-13, rtol=1e-14)
+
+
+def schwarzschild_swept_to(b, r0, r1):
+    """Orbital angle a plunging photon (b < 3 sqrt 3) sweeps from r0 in to r1."""
+    def g(r):
+        return 1.0 / (r * r * math.sqrt(1.0 / (b * b) - (1.0 - 2.0 / r) / (r * r)))
+    return integrate.quad(g, r1, r0, epsabs=1e-13, epsrel=1e-13, limit=400)[0]
