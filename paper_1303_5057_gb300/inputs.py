@@ -47,7 +47,9 @@ def uniform(seed: int, n: int, lo: float = 0.0, hi: float = 1.0, offset: int = 0
 class Image:
     """One image request: a black hole of spin ``a`` seen by an observer at
     ``r_obs`` and inclination ``incl`` (radians), through an nx x ny pixel grid
-    over [alpha0, alpha1] x [beta0, beta1] (units of M)."""
+    over [alpha0, alpha1] x [beta0, beta1] (units of M).  grid = 1 makes it
+    the polar grid of the ring study instead: nx radii cell-centred on
+    (alpha0, alpha1), ny angles from beta0 to beta1 inclusive."""
     a: float
     incl: float
     nx: int
@@ -58,6 +60,7 @@ class Image:
     alpha1: float = 10.0
     beta0: float = -10.0
     beta1: float = 10.0
+    grid: int = 0
 
     @property
     def n(self) -> int:
@@ -104,6 +107,31 @@ def shadow_sweep(n_images: int = 256, side_lo: int = 64, side_hi: int = 1024,
                  ny=int(side[k])) for k in range(n_images)]
     return Workload("shadow_sweep_%d" % n_images, ims, precision="fp32_kahan_sel64",
                     max_steps=10000)
+
+
+def polar_image(a: float, incl_deg: float, n_R: int = 6000, n_th: int = 181, R0: float = 1.5,
+                R1: float = 7.5, th0: float = 0.0, th1: float = math.pi, r_obs: float = 1000.0) -> Image:
+    """One image of the Sec. 4 ring study: the polar grid of n_R radii over
+    (R0, R1) by n_th angles over [th0, th1] (the paper's 6000 x 181 over
+    (1.5, 7.5) M x [0, pi]), observer at r_obs and inclination incl_deg."""
+    return Image(a=float(a), incl=math.radians(float(incl_deg)), nx=int(n_R), ny=int(n_th), r_obs=r_obs,
+                 alpha0=R0, alpha1=R1, beta0=th0, beta1=th1, grid=1)
+
+
+def ring_spins():
+    """The 16 spins of the ring study, a_j = 1 - 10^(-j/5), j = 0..15."""
+    return [1.0 - 10.0 ** (-j / 5.0) for j in range(16)]
+
+
+def ring_sweep(n_R: int = 6000, n_th: int = 181, spins=None, incls_deg=None):
+    """Sec. 4 parameter study: 16 spins x 19 inclinations (0, 5, .., 90 deg),
+    each a polar image of n_R x n_th rays (3.3e8 rays at the paper's size).
+    Deterministic; no random draws."""
+    spins = ring_spins() if spins is None else list(spins)
+    incls = list(range(0, 91, 5)) if incls_deg is None else list(incls_deg)
+    ims = [polar_image(a, i, n_R, n_th) for a in spins for i in incls]
+    return Workload("ring_sweep_%dx%dx%dx%d" % (len(spins), len(incls), n_R, n_th), ims,
+                    precision="fp32_kahan_sel64", max_steps=100000)
 
 
 def _bardeen_point(a, incl, u):
