@@ -71,11 +71,14 @@ def parse_args():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-rays", type=int, default=16384)
     p.add_argument("--workload", default="kerr1024",
-                   choices=["kerr1024", "schwarzschild64", "mixed", "sweep", "serve", "projection"])
+                   choices=["kerr1024", "schwarzschild64", "mixed", "sweep", "serve", "projection", "rings"])
     p.add_argument("--rays", type=int, default=1 << 22, help="mixed workload: rays")
     p.add_argument("--images", type=int, default=256, help="sweep workload: images")
     p.add_argument("--rates", default="10,30,100,300,1000", help="serve workload: req/s")
     p.add_argument("--requests", type=int, default=200, help="serve workload: requests per rate")
+    p.add_argument("--ring-nr", type=int, default=6000, help="rings workload: radii per angle")
+    p.add_argument("--ring-nth", type=int, default=181, help="rings workload: angles")
+    p.add_argument("--ring-out", default="", help="rings workload: write the per-image table here (JSON)")
     return p.parse_args()
 
 
@@ -351,6 +354,64 @@ def run_projection(args):
     return 0
 
 
+def run_rings(args):
+    """Sec. 4 ring study: 16 spins x 19 inclinations, each a polar image of
+    ring-nr x ring-nth rays (3.3e8 rays at the paper's 6000 x 181), set up,
+    planned, traced in one persistent launch (Eq. 2 step rule, compensated
+    FP32 with double steps near the hole) and reduced to D, <R>, A per image.
+    The timed region is the whole study, inputs generated on the device."""
+    import torch
+    from paper_1303_5057_gb300 import gray
+    from paper_1303_5057_gb300 import inputs as I
+    wl = I.ring_sweep(args.ring_nr, args.ring_nth)
+    ims = wl.images
+    opt = gray.Options(precision=gray.FP32_KAHAN_SEL64, step_rule=gray.STEP_EQ2, h_min=1e-9, max_steps=100000,
+                       r_sw=args.r_sw, block=args.block, blocks_per_sm=args.blocks_per_sm, refill=args.refill)
+    tr = gray.Tracer(opt, wl.n_rays)
+    rows = sum(im.ny for im in ims)
+    order = torch.empty(wl.n_rays, dtype=torch.int32, device="cuda")
+    info = torch.empty(gray.RING_DTYPE.itemsize * len(ims), dtype=torch.uint8, device="cuda")
+    bnd = torch.empty(rows, dtype=torch.float64, device="cuda")
+    gray.gray_set_timing(tr.ctx, True)
+    launches0 = gray.gray_launch_count()
+
+    def step():
+        tr.setup(ims)
+        q = order
+        if not args.no_plan:
+            q = tr.plan(ims, probe_stride=args.probe_stride, probe_budget=args.probe_budget, order=order)
+        _, _, st = tr.trace(order=None if args.no_plan else q)
+        gray.gray_ring(tr.ctx, tr.state, tr.n, ims, out=info, boundary=bnd)
+        return st
+    step()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    reps = max(1, min(args.steps, 2))
+    launches1 = gray.gray_launch_count()
+    ms, st = _timed(step, reps)
+    launches = (gray.gray_launch_count() - launches1) // reps
+    clk = clocks.stop()
+    passes = gray.gray_timings(tr.ctx)
+    r = gray.as_numpy(info, gray.RING_DTYPE)
+    tr.close()
+    table = [{"a": im.a, "incl_deg": round(math.degrees(im.incl), 6), "D": float(x["D"]), "R_mean": float(x["R_mean"]),
+              "A": float(x["A"]), "n_wrong": int(x["n_wrong"]), "n_open": int(x["n_open"])}
+             for im, x in zip(ims, r)]
+    if args.ring_out:
+        with open(args.ring_out, "w") as f:
+            json.dump(table, f)
+    print(json.dumps({"workload": wl.name, "images": len(ims), "rays": wl.n_rays,
+                      "metric": "photon RK4 steps/s", "unit": UNIT, "value": st[0] / (ms / 1000.0),
+                      "ms_per_study": ms, "steps": st[0], "fp64_steps": st[2], "euler": st[1],
+                      "ns_per_photon_step": 1e6 * ms / st[0], "gpu_launches": launches,
+                      "passes_ms": passes, "queue": "natural" if args.no_plan else "planned",
+                      "R_mean_range": [float(r["R_mean"].min()), float(r["R_mean"].max())],
+                      "A_max": float(r["A"].max()), "D_max": float(r["D"].max()),
+                      "wrong_rays": int(r["n_wrong"].sum()), "open_rows": int(r["n_open"].sum()),
+                      "clocks": clk}), flush=True)
+    return 0
+
+
 # --------------------------------------------------------------- GPU arm ---
 
 def main():
@@ -364,7 +425,7 @@ def main():
         build.build()
         gray.lib()
         return {"schwarzschild64": run_schwarzschild64, "mixed": run_mixed, "sweep": run_sweep,
-                "serve": run_serve, "projection": run_projection}[args.workload](args)
+                "serve": run_serve, "projection": run_projection, "rings": run_rings}[args.workload](args)
 
     import torch
 

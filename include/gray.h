@@ -78,18 +78,33 @@ extern "C" {
 #define GRAY_LAUNCH_PERSISTENT 0     /* persistent warps refilled from a work queue (default) */
 #define GRAY_LAUNCH_ONE_PER_THREAD 1 /* the paper's launch (Eq. 1): one ray per thread, blocks of 64, no refill */
 
+/* ---- image-plane grids (gray_image.grid) ------------------------------ */
+#define GRAY_GRID_CARTESIAN 0 /* pixel centres of an nx x ny grid over [alpha0, alpha1] x [beta0, beta1] */
+#define GRAY_GRID_POLAR 1     /* Sec. 4's polar grid: nx radii x ny angles, see gray_image */
+
 /* One image: a hole of spin a and mass M seen by an observer at distance
- * r_obs and inclination incl, through an nx x ny grid of pixel centres
- * alpha_j = alpha0 + (j + 1/2)(alpha1 - alpha0)/nx (beta likewise) on the
- * image plane (Sec. 4 sets the plane at r = 1000 M).  Ray index within the
- * image is row * nx + column, rows along beta. */
+ * r_obs and inclination incl, through a grid of rays on the image plane
+ * (Sec. 4 sets the plane at r = 1000 M).  Ray index within the image is
+ * row * nx + column.
+ *
+ * GRAY_GRID_CARTESIAN: pixel centres alpha_j = alpha0 + (j + 1/2)(alpha1 -
+ *   alpha0)/nx, beta_i = beta0 + (i + 1/2)(beta1 - beta0)/ny; rows along beta.
+ * GRAY_GRID_POLAR (the ring study of Sec. 4, Eqs. 9-10): columns are radii
+ *   R_j = alpha0 + (j + 1/2)(alpha1 - alpha0)/nx, cell-centred on the open
+ *   interval (alpha0, alpha1), 0 <= alpha0 < alpha1; rows are angles
+ *   vartheta_i = beta0 + i (beta1 - beta0)/(ny - 1), both ends included
+ *   (vartheta = beta0 when ny = 1); the ray sits at alpha = R cos vartheta,
+ *   beta = R sin vartheta.  The paper's grid is nx = 6000 over (1.5, 7.5) M,
+ *   ny = 181 over [0, pi]. */
 typedef struct gray_image {
     double a;        /* spin; |a| < M when M > 0, any |a| when M = 0 (flat space) */
     double M;        /* mass, >= 0 */
     double r_obs;    /* distance of the image plane, > 0 */
     double incl;     /* observer inclination, radians, [0, pi] */
-    int32_t nx, ny;  /* pixels, >= 1 each */
-    double alpha0, alpha1, beta0, beta1; /* window on the image plane */
+    int32_t nx, ny;  /* rays per row and rows, >= 1 each */
+    double alpha0, alpha1, beta0, beta1; /* window (Cartesian) or radial and angular range (polar) */
+    int32_t grid;     /* GRAY_GRID_CARTESIAN (0) or GRAY_GRID_POLAR */
+    int32_t reserved; /* must be 0 */
 } gray_image;
 
 /* Integration options (Sec. 2 parameters plus the GPU launch shape). */
@@ -249,10 +264,52 @@ int gray_count_active(gray_ctx *ctx, const void *state_dev, size_t state_bytes, 
  * captured pixels on the image plane, equivalent radius sqrt(area/pi) and
  * centroid (the quantities from which Sec. 4 builds its ring metrics).
  * out_dev receives n_images gray_shadow_info records (out_bytes bytes).
+ * Cartesian images only (a polar image is GRAY_EINVAL).
  * Errors: GRAY_EINVAL, GRAY_ECUDA. */
 int gray_shadow(gray_ctx *ctx, const void *state_dev, size_t state_bytes, int64_t n_state,
                 int64_t first_ray, const gray_image *images_host, int32_t n_images,
                 gray_shadow_info *out_dev, size_t out_bytes, void *stream);
+
+/* Photon ring of each of n_images polar images (GRAY_GRID_POLAR) whose rays
+ * start at first_ray, traced to completion: the ring metrics of Sec. 4.
+ *
+ * Boundary of each angle row: the cell edge R_b = alpha0 + k dR (k = 0..nx,
+ * dR = (alpha1 - alpha0)/nx) that leaves the fewest of the row's rays on the
+ * wrong side (captured outside it, or not captured inside it); with C(k) the
+ * captured count among the k innermost rays, k maximises 2 C(k) - k, ties to
+ * the smallest k.  For a row whose captured rays are exactly its innermost
+ * ones this is the midpoint between the last captured and the first
+ * uncaptured ray; isolated misclassified rays away from the boundary do not
+ * move it.  From the boundary points alpha_0 = R_b cos vartheta, beta_0 =
+ * R_b sin vartheta (Eqs. 9-10): alpha_min and alpha_max over the rows,
+ * centre c = (alpha_min + alpha_max)/2, D = |c| (Eq. 6), R = |(alpha_0 - c,
+ * beta_0)|, <R> (Eq. 7) and A = 2 sqrt(mean (R - <R>)^2) (Eq. 8), where the
+ * means over vartheta are trapezoidal over the rows' angles divided by their
+ * span (over [0, pi] this is the full-circle mean of Eqs. 7-8, the image being
+ * symmetric under beta -> -beta).
+ *
+ * out_dev receives n_images gray_ring_info records (out_bytes bytes);
+ * boundary_dev, if not NULL, receives each image's ny boundary radii R_b,
+ * images one after another (boundary_bytes >= 8 * total rows).  Rays still
+ * ACTIVE count as not captured.  Integer counts are exact; the metrics are
+ * computed in double in a fixed order (bitwise reproducible).
+ * Errors: GRAY_EINVAL (NULL or short buffers, a Cartesian image, rays outside
+ * the buffer), GRAY_ECUDA. */
+typedef struct gray_ring_info {
+    double D;                    /* Eq. 6 */
+    double R_mean;               /* Eq. 7 */
+    double A;                    /* Eq. 8 */
+    double alpha_min, alpha_max; /* horizontal extent of the sampled ring */
+    int64_t n_captured;          /* captured rays of the image */
+    int64_t n_wrong;             /* rays on the wrong side of their row's boundary */
+    int32_t n_open;              /* rows whose boundary is an end of the radial range (k = 0 or nx) */
+    int32_t n_rows;              /* rows (ny) */
+} gray_ring_info;
+
+int gray_ring(gray_ctx *ctx, const void *state_dev, size_t state_bytes, int64_t n_state,
+              int64_t first_ray, const gray_image *images_host, int32_t n_images,
+              gray_ring_info *out_dev, size_t out_bytes, double *boundary_dev, size_t boundary_bytes,
+              void *stream);
 
 /* Maximum number of images one gray_setup_noalloc call accepts. */
 #define GRAY_NOALLOC_MAX_IMAGES 4096
@@ -267,8 +324,8 @@ int gray_shadow(gray_ctx *ctx, const void *state_dev, size_t state_bytes, int64_
  *
  * It writes the same initial states as gray_setup (bit for bit) for a
  * buffer laid out for `precision`.  The image table is copied into a
- * file-scope device array of GRAY_NOALLOC_MAX_IMAGES entries (80 bytes each,
- * 320 KB) that every device loading the library holds until the process
+ * file-scope device array of GRAY_NOALLOC_MAX_IMAGES entries (88 bytes each,
+ * 352 KB) that every device loading the library holds until the process
  * exits; n_images above that maximum is rejected with GRAY_EINVAL before any
  * work is enqueued.  On the first call on a device the library looks up that
  * array's device address (cudaGetSymbolAddress) with the device current and

@@ -179,10 +179,30 @@ namespace {
 // --------------------------------------------------------------------------
 
 struct ImageDev {
-    double a, M, r_obs, incl, a0, da, b0, db;
+    double a, M, r_obs, incl;
+    double a0, da; // Cartesian: alpha of the first pixel edge, pixel width; polar: R0, dR
+    double b0, db; // Cartesian: beta likewise; polar: first angle, angle step
     long long first; // first ray of the image relative to the call's first ray
     int nx, ny;
+    int grid, pad;
 };
+
+// Image-plane position of the ray in (row, col) of an image: a pixel centre
+// of the Cartesian grid, or the polar grid point of Sec. 4 (Eqs. 9-10).
+__device__ __forceinline__ void image_point(const ImageDev &im, int64_t row, int64_t col, double &alpha,
+                                            double &beta)
+{
+    if (im.grid == GRAY_GRID_POLAR) {
+        const double R = im.a0 + ((double)col + 0.5) * im.da;
+        double s, c;
+        sincos(im.b0 + (double)row * im.db, &s, &c);
+        alpha = R * c;
+        beta = R * s;
+    } else {
+        alpha = im.a0 + ((double)col + 0.5) * im.da;
+        beta = im.b0 + ((double)row + 0.5) * im.db;
+    }
+}
 
 // Store one initial state (double) into the layout of `prec`.  FP32 modes keep
 // the rounding error of each component in the compensation plane, so a
@@ -232,8 +252,8 @@ __global__ void setup_images_kernel(const ImageDev *imgs, int n_images, int64_t 
     const ImageDev im = imgs[lo];
     const int64_t p = i - im.first;
     const int64_t row = p / im.nx, col = p - row * im.nx;
-    const double alpha = im.a0 + ((double)col + 0.5) * im.da;
-    const double beta = im.b0 + ((double)row + 0.5) * im.db;
+    double alpha, beta;
+    image_point(im, row, col, alpha, beta);
     double y[8];
     initial_state(im.M, im.a, im.r_obs, im.incl, alpha, beta, y);
     store_initial(v, prec, first_ray + i, y, im.a, im.M, im.r_obs);
@@ -1221,6 +1241,159 @@ __global__ void shadow_final_kernel(const ImageDev *imgs, int n_images, gray_sha
 }
 
 // --------------------------------------------------------------------------
+// Photon-ring metrics of polar images (Sec. 4, Eqs. 6-10)
+// --------------------------------------------------------------------------
+
+struct RingDev {
+    long long first;     // first ray of the image relative to the call's first ray
+    long long first_row; // first boundary row of the image
+    int nx, ny;
+    double R0, dR, th0, dth;
+};
+
+constexpr int RING_BLOCK = 256;
+constexpr int RING_PER_THREAD = 16;
+constexpr int RING_TILE = RING_BLOCK * RING_PER_THREAD;
+
+// (score, k) packed so that the larger key has the larger score and, among
+// equal scores, the smaller k (0 <= k < 2^31).
+__device__ __forceinline__ long long ring_key(long long score, int k)
+{
+    return score * 4294967296LL + (long long)(4294967295u - (unsigned)k);
+}
+
+// One block per angle row.  The row's statuses are staged tile by tile in
+// shared memory with coalesced loads; each thread owns 16 consecutive rays
+// of a tile, a block scan gives the captured count before them, and each
+// thread walks its rays tracking the best boundary k (the largest
+// 2 C(k) - k, ties to the smallest k).  Boundary, captured count, rays on
+// the wrong side and open rows go to the row's image with integer atomics.
+__global__ void __launch_bounds__(RING_BLOCK) ring_rows_kernel(const int4 *S0, int64_t first_ray,
+                                                                const RingDev *imgs, int n_images,
+                                                                double *boundary, gray_ring_info *out)
+{
+    __shared__ unsigned char cap[RING_TILE];
+    __shared__ int s_cnt[RING_BLOCK / 32];
+    __shared__ long long s_key[RING_BLOCK / 32];
+    const long long row = blockIdx.x;
+    int lo = 0, hi = n_images - 1;
+    while (lo < hi) { // last image with first_row <= row
+        const int mid = (lo + hi + 1) >> 1;
+        if (imgs[mid].first_row <= row)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const RingDev im = imgs[lo];
+    const int64_t base = first_ray + im.first + (row - im.first_row) * (int64_t)im.nx;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    long long carry = 0;                 // captured rays before the tile
+    long long best = ring_key(0, 0);     // k = 0: nothing inside
+    for (int t0 = 0; t0 < im.nx; t0 += RING_TILE) {
+        const int len = min(RING_TILE, im.nx - t0);
+        for (int e = tid; e < len; e += RING_BLOCK)
+            cap[e] = (unsigned char)(S0[base + t0 + e].x == GRAY_RAY_CAPTURED);
+        __syncthreads();
+        const int e0 = tid * RING_PER_THREAD, e1 = min(e0 + RING_PER_THREAD, len);
+        int cnt = 0;
+        for (int e = e0; e < e1; ++e)
+            cnt += cap[e];
+        // block exclusive scan of cnt
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o)
+                incl += v;
+        }
+        if (lane == 31)
+            s_cnt[warp] = incl;
+        __syncthreads();
+        int before = 0, tile_total = 0;
+        for (int w = 0; w < RING_BLOCK / 32; ++w) {
+            if (w < warp)
+                before += s_cnt[w];
+            tile_total += s_cnt[w];
+        }
+        long long C = carry + before + (incl - cnt);
+        long long mine = best;
+        for (int e = e0; e < e1; ++e) {
+            C += cap[e];
+            const int k = t0 + e + 1;
+            const long long key = ring_key(2 * C - k, k);
+            mine = key > mine ? key : mine;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long v = __shfl_xor_sync(0xffffffffu, mine, o);
+            mine = v > mine ? v : mine;
+        }
+        if (lane == 0)
+            s_key[warp] = mine;
+        __syncthreads();
+        for (int w = 0; w < RING_BLOCK / 32; ++w)
+            best = s_key[w] > best ? s_key[w] : best;
+        carry += tile_total;
+        __syncthreads(); // cap, s_cnt and s_key are rewritten by the next tile
+    }
+    if (tid == 0) {
+        const int k = (int)(4294967295u - (unsigned)(best & 0xffffffffLL));
+        const long long score = (best - (long long)(4294967295u - (unsigned)k)) / 4294967296LL;
+        const long long Ck = (score + k) / 2;
+        boundary[row] = __dadd_rn(im.R0, __dmul_rn((double)k, im.dR)); // no contraction: R0 + k dR as written
+        gray_ring_info *o = out + lo;
+        atomicAdd((unsigned long long *)&o->n_captured, (unsigned long long)carry);
+        atomicAdd((unsigned long long *)&o->n_wrong, (unsigned long long)((k - Ck) + (carry - Ck)));
+        if (k == 0 || k == im.nx)
+            atomicAdd(&o->n_open, 1);
+    }
+}
+
+// Eqs. 6-8 from each image's boundary rows, one thread per image, in a fixed
+// order: extremes of alpha_0 = R_b cos(vartheta), centre, then trapezoidal
+// means over the rows' angles of R and of (R - <R>)^2.
+__global__ void ring_final_kernel(const RingDev *imgs, int n_images, const double *boundary, gray_ring_info *out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_images)
+        return;
+    const RingDev im = imgs[k];
+    const double *Rb = boundary + im.first_row;
+    double a_min = 0.0, a_max = 0.0;
+    for (int j = 0; j < im.ny; ++j) {
+        double sn, cs;
+        sincos(im.th0 + (double)j * im.dth, &sn, &cs);
+        const double al = Rb[j] * cs;
+        a_min = (j == 0 || al < a_min) ? al : a_min;
+        a_max = (j == 0 || al > a_max) ? al : a_max;
+    }
+    const double c = 0.5 * (a_min + a_max);
+    double sum = 0.0, wsum = 0.0;
+    for (int j = 0; j < im.ny; ++j) {
+        double sn, cs;
+        sincos(im.th0 + (double)j * im.dth, &sn, &cs);
+        const double R = sqrt((Rb[j] * cs - c) * (Rb[j] * cs - c) + (Rb[j] * sn) * (Rb[j] * sn));
+        const double w = (im.ny > 1 && (j == 0 || j == im.ny - 1)) ? 0.5 : 1.0;
+        sum += w * R;
+        wsum += w;
+    }
+    const double R_mean = sum / wsum;
+    double var = 0.0;
+    for (int j = 0; j < im.ny; ++j) {
+        double sn, cs;
+        sincos(im.th0 + (double)j * im.dth, &sn, &cs);
+        const double R = sqrt((Rb[j] * cs - c) * (Rb[j] * cs - c) + (Rb[j] * sn) * (Rb[j] * sn));
+        const double w = (im.ny > 1 && (j == 0 || j == im.ny - 1)) ? 0.5 : 1.0;
+        var += w * (R - R_mean) * (R - R_mean);
+    }
+    gray_ring_info *o = out + k;
+    o->D = fabs(c);
+    o->R_mean = R_mean;
+    o->A = 2.0 * sqrt(var / wsum);
+    o->alpha_min = a_min;
+    o->alpha_max = a_max;
+    o->n_rows = im.ny;
+}
+
+// --------------------------------------------------------------------------
 // Unit evaluations for parity tests
 // --------------------------------------------------------------------------
 
@@ -1325,8 +1498,17 @@ int validate_image(const gray_image &im)
         return GRAY_EINVAL;
     if (im.incl < 0 || im.incl > 3.14159265358979323846)
         return GRAY_EINVAL;
-    if (!(im.alpha1 != im.alpha0) || !(im.beta1 != im.beta0))
+    if (im.reserved != 0)
         return GRAY_EINVAL;
+    if (im.grid == GRAY_GRID_POLAR) {
+        if (!(im.alpha0 >= 0) || !(im.alpha1 > im.alpha0) || (im.ny > 1 && !(im.beta1 != im.beta0)))
+            return GRAY_EINVAL;
+    } else if (im.grid == GRAY_GRID_CARTESIAN) {
+        if (!(im.alpha1 != im.alpha0) || !(im.beta1 != im.beta0))
+            return GRAY_EINVAL;
+    } else {
+        return GRAY_EINVAL;
+    }
     return GRAY_OK;
 }
 
@@ -1342,25 +1524,37 @@ int check_state(const gray_ctx *ctx, const void *state, size_t state_bytes, int6
 
 unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
+// Device description of one (validated) image whose rays start `first` rays
+// into the call's range.
+ImageDev image_dev(const gray_image &im, int64_t first)
+{
+    ImageDev d;
+    d.a = im.a;
+    d.M = im.M;
+    d.r_obs = im.r_obs;
+    d.incl = im.incl;
+    d.a0 = im.alpha0;
+    d.da = (im.alpha1 - im.alpha0) / im.nx;
+    d.b0 = im.beta0;
+    if (im.grid == GRAY_GRID_POLAR)
+        d.db = im.ny > 1 ? (im.beta1 - im.beta0) / (im.ny - 1) : 0.0;
+    else
+        d.db = (im.beta1 - im.beta0) / im.ny;
+    d.first = first;
+    d.nx = im.nx;
+    d.ny = im.ny;
+    d.grid = im.grid;
+    d.pad = 0;
+    return d;
+}
+
 std::vector<ImageDev> image_table(const gray_image *images, int n_images, int64_t &total)
 {
     std::vector<ImageDev> t((size_t)n_images);
     total = 0;
     for (int k = 0; k < n_images; ++k) {
-        const gray_image &im = images[k];
-        ImageDev &d = t[(size_t)k];
-        d.a = im.a;
-        d.M = im.M;
-        d.r_obs = im.r_obs;
-        d.incl = im.incl;
-        d.a0 = im.alpha0;
-        d.da = (im.alpha1 - im.alpha0) / im.nx;
-        d.b0 = im.beta0;
-        d.db = (im.beta1 - im.beta0) / im.ny;
-        d.nx = im.nx;
-        d.ny = im.ny;
-        d.first = total;
-        total += (int64_t)im.nx * im.ny;
+        t[(size_t)k] = image_dev(images[k], total);
+        total += (int64_t)images[k].nx * images[k].ny;
     }
     return t;
 }
@@ -1862,6 +2056,9 @@ int gray_shadow(gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_
         return rc;
     if (!images || n_images < 1 || first_ray < 0 || !out || out_bytes < sizeof(gray_shadow_info) * (size_t)n_images)
         return GRAY_EINVAL;
+    for (int k = 0; k < n_images; ++k)
+        if ((rc = validate_image(images[k])) || images[k].grid != GRAY_GRID_CARTESIAN)
+            return GRAY_EINVAL;
     int64_t total = 0;
     std::vector<ImageDev> t = image_table(images, n_images, total);
     if (first_ray + total > n_state)
@@ -1880,6 +2077,66 @@ int gray_shadow(gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_
     shadow_final_kernel<<<grid_for(n_images, 128), 128, 0, s>>>((const ImageDev *)dimg, n_images, out);
     rc = check_launch();
     cudaError_t e = cudaFreeAsync(dimg, s);
+    if (rc)
+        return rc;
+    return cuda_err(e);
+}
+
+int gray_ring(gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_state, int64_t first_ray,
+              const gray_image *images, int32_t n_images, gray_ring_info *out, size_t out_bytes, double *boundary,
+              size_t boundary_bytes, void *stream)
+{
+    int rc = check_state(ctx, state, state_bytes, n_state);
+    if (rc)
+        return rc;
+    if (!images || n_images < 1 || first_ray < 0 || !out || out_bytes < sizeof(gray_ring_info) * (size_t)n_images)
+        return GRAY_EINVAL;
+    std::vector<RingDev> t((size_t)n_images);
+    int64_t total = 0, rows = 0;
+    for (int k = 0; k < n_images; ++k) {
+        const gray_image &im = images[k];
+        if ((rc = validate_image(im)) || im.grid != GRAY_GRID_POLAR)
+            return GRAY_EINVAL;
+        const ImageDev d = image_dev(im, total);
+        RingDev &r = t[(size_t)k];
+        r.first = total;
+        r.first_row = rows;
+        r.nx = im.nx;
+        r.ny = im.ny;
+        r.R0 = d.a0;
+        r.dR = d.da;
+        r.th0 = d.b0;
+        r.dth = d.db;
+        total += (int64_t)im.nx * im.ny;
+        rows += im.ny;
+    }
+    if (first_ray + total > n_state || rows > 0x7fffffff)
+        return GRAY_EINVAL;
+    if (boundary && boundary_bytes < sizeof(double) * (size_t)rows)
+        return GRAY_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    // one stream-ordered scratch block: the image table, then (without a
+    // caller buffer) the boundary rows
+    const size_t table_bytes = (sizeof(RingDev) * t.size() + 255) & ~(size_t)255;
+    const size_t scratch = table_bytes + (boundary ? 0 : sizeof(double) * (size_t)rows);
+    void *dmem = nullptr;
+    if (cudaMallocAsync(&dmem, scratch, s) != cudaSuccess)
+        return GRAY_ECUDA;
+    const RingDev *dimg = (const RingDev *)dmem;
+    double *rb = boundary ? boundary : (double *)((char *)dmem + table_bytes);
+    if (cudaMemcpyAsync(dmem, t.data(), sizeof(RingDev) * t.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(out, 0, sizeof(gray_ring_info) * (size_t)n_images, s) != cudaSuccess) {
+        cudaFreeAsync(dmem, s);
+        return GRAY_ECUDA;
+    }
+    const StateView v = make_view((void *)state, n_state, ctx->opt.precision);
+    ring_rows_kernel<<<(unsigned)rows, RING_BLOCK, 0, s>>>(v.S0, first_ray, dimg, n_images, rb, out);
+    rc = check_launch();
+    if (!rc) {
+        ring_final_kernel<<<grid_for(n_images, 128), 128, 0, s>>>(dimg, n_images, rb, out);
+        rc = check_launch();
+    }
+    cudaError_t e = cudaFreeAsync(dmem, s);
     if (rc)
         return rc;
     return cuda_err(e);
@@ -1951,18 +2208,7 @@ int gray_setup_noalloc(int32_t precision, const gray_image *images, int32_t n_im
         const int m = (n_images - k0) < kChunk ? (n_images - k0) : kChunk;
         for (int j = 0; j < m; ++j) {
             const gray_image &im = images[k0 + j];
-            ImageDev &d = chunk[j];
-            d.a = im.a;
-            d.M = im.M;
-            d.r_obs = im.r_obs;
-            d.incl = im.incl;
-            d.a0 = im.alpha0;
-            d.da = (im.alpha1 - im.alpha0) / im.nx;
-            d.b0 = im.beta0;
-            d.db = (im.beta1 - im.beta0) / im.ny;
-            d.nx = im.nx;
-            d.ny = im.ny;
-            d.first = first;
+            chunk[j] = image_dev(im, first);
             first += (int64_t)im.nx * im.ny;
         }
         if (cudaMemcpyAsync((ImageDev *)table + k0, chunk, sizeof(ImageDev) * (size_t)m, cudaMemcpyHostToDevice,

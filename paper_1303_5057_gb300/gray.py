@@ -27,6 +27,7 @@ STEP_BENCH, STEP_EQ2 = 0, 1
 RENDER_PIXELS64, RENDER_PIXELS32, RENDER_RECORD, RENDER_INVARIANTS = 0, 1, 3, 4
 EVAL_CHRISTOFFEL, EVAL_RHS, EVAL_INITIAL, EVAL_XI, EVAL_SINCOS = 0, 1, 2, 3, 4
 LAUNCH_PERSISTENT, LAUNCH_ONE_PER_THREAD = 0, 1
+GRID_CARTESIAN, GRID_POLAR = 0, 1
 RECORD = 17
 NOALLOC_MAX_IMAGES = 4096
 
@@ -50,13 +51,15 @@ class _Options(C.Structure):
 class _Image(C.Structure):
     _fields_ = [("a", C.c_double), ("M", C.c_double), ("r_obs", C.c_double), ("incl", C.c_double),
                 ("nx", C.c_int32), ("ny", C.c_int32), ("alpha0", C.c_double), ("alpha1", C.c_double),
-                ("beta0", C.c_double), ("beta1", C.c_double)]
+                ("beta0", C.c_double), ("beta1", C.c_double), ("grid", C.c_int32), ("reserved", C.c_int32)]
 
 
 SHADOW_DTYPE = np.dtype([("n_captured", "<i8"), ("n_escaped", "<i8"), ("n_other", "<i8"),
                          ("area", "<f8"), ("radius", "<f8"), ("alpha_c", "<f8"), ("beta_c", "<f8")])
 PIXEL64_DTYPE = np.dtype([("r", "<f8"), ("theta", "<f8"), ("phi", "<f8"), ("status", "<i4"), ("steps", "<i4")])
 PIXEL32_DTYPE = np.dtype([("r", "<f4"), ("theta", "<f4"), ("phi", "<f4"), ("status", "<i4")])
+RING_DTYPE = np.dtype([("D", "<f8"), ("R_mean", "<f8"), ("A", "<f8"), ("alpha_min", "<f8"), ("alpha_max", "<f8"),
+                       ("n_captured", "<i8"), ("n_wrong", "<i8"), ("n_open", "<i4"), ("n_rows", "<i4")])
 
 
 @dataclass
@@ -121,6 +124,8 @@ def lib():
     L.gray_render.restype = C.c_int
     L.gray_shadow.argtypes = [vp, vp, sz, i64, i64, C.POINTER(_Image), i32, vp, sz, vp]
     L.gray_shadow.restype = C.c_int
+    L.gray_ring.argtypes = [vp, vp, sz, i64, i64, C.POINTER(_Image), i32, vp, sz, vp, sz, vp]
+    L.gray_ring.restype = C.c_int
     L.gray_eval.argtypes = [i32, i32, vp, i64, vp, vp]
     L.gray_eval.restype = C.c_int
     L.gray_set_timing.argtypes = [vp, i32]
@@ -166,7 +171,7 @@ def _images(images):
     for k, im in enumerate(images):
         arr[k] = _Image(float(im.a), float(getattr(im, "M", 1.0)), float(im.r_obs), float(im.incl),
                         int(im.nx), int(im.ny), float(im.alpha0), float(im.alpha1),
-                        float(im.beta0), float(im.beta1))
+                        float(im.beta0), float(im.beta1), int(getattr(im, "grid", GRID_CARTESIAN)), 0)
     return arr
 
 
@@ -314,6 +319,22 @@ def gray_shadow(ctx, state, n_state, images, first_ray=0, out=None, stream=None)
     return out
 
 
+def gray_ring(ctx, state, n_state, images, first_ray=0, out=None, boundary=None, stream=None):
+    """Ring metrics (Sec. 4) of traced polar images: a uint8 CUDA tensor of
+    len(images) RING_DTYPE records.  ``boundary``: optional float64 CUDA
+    tensor that receives every image's boundary radius per angle row."""
+    import torch
+    arr = _images(images)
+    if out is None:
+        out = torch.empty(RING_DTYPE.itemsize * len(images), dtype=torch.uint8, device=state.device)
+    bp = _ptr(boundary) if boundary is not None else None
+    bb = boundary.numel() * boundary.element_size() if boundary is not None else 0
+    _check(lib().gray_ring(ctx, _ptr(state), state.numel() * state.element_size(), int(n_state),
+                           int(first_ray), arr, len(images), _ptr(out), out.numel() * out.element_size(),
+                           bp, bb, _stream(stream)), "gray_ring")
+    return out
+
+
 def gray_eval(what, precision, inp, stream=None):
     """inp: float64 CUDA tensor of n rows (4, 10, 6 or 10 doubles by ``what``).
     Returns a float64 CUDA tensor of n rows (64, 8, 8 or 1 doubles)."""
@@ -390,3 +411,17 @@ class Tracer:
         import torch
         torch.cuda.synchronize()
         return as_numpy(t, SHADOW_DTYPE)
+
+    def ring(self, images, first_ray=0):
+        """(RING_DTYPE records, boundary radii per image as a list of arrays)."""
+        import torch
+        rows = sum(int(im.ny) for im in images)
+        b = torch.empty(max(1, rows), dtype=torch.float64, device=self.state.device)
+        t = gray_ring(self.ctx, self.state, self.n, images, first_ray, boundary=b)
+        torch.cuda.synchronize()
+        bh = b.cpu().numpy()
+        out, k = [], 0
+        for im in images:
+            out.append(bh[k:k + int(im.ny)])
+            k += int(im.ny)
+        return as_numpy(t, RING_DTYPE), out
