@@ -58,7 +58,9 @@ def parse_args():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gray", choices=["gray", "reference"])
     p.add_argument("--side", type=int, default=1024)
-    p.add_argument("--precision", default="fp32_kahan_sel64")
+    p.add_argument("--precision", default=None,
+                   help="fp64 | fp32 | fp32_kahan | fp32_kahan_sel64 (default: fp32_kahan for the ring study, "
+                        "whose result is the capture map alone, else fp32_kahan_sel64)")
     p.add_argument("--r-sw", type=float, default=0.02)
     p.add_argument("--step-rule", default="bench", choices=["bench", "eq2"])
     p.add_argument("--block", type=int, default=0)
@@ -71,7 +73,7 @@ def parse_args():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-rays", type=int, default=16384)
     p.add_argument("--workload", default="kerr1024",
-                   choices=["kerr1024", "schwarzschild64", "mixed", "sweep", "serve", "projection", "rings"])
+                   choices=["kerr1024", "schwarzschild64", "mixed", "sweep", "serve", "projection", "rings", "view"])
     p.add_argument("--rays", type=int, default=1 << 22, help="mixed workload: rays")
     p.add_argument("--images", type=int, default=256, help="sweep workload: images")
     p.add_argument("--rates", default="10,30,100,300,1000", help="serve workload: req/s")
@@ -79,6 +81,8 @@ def parse_args():
     p.add_argument("--ring-nr", type=int, default=6000, help="rings workload: radii per angle")
     p.add_argument("--ring-nth", type=int, default=181, help="rings workload: angles")
     p.add_argument("--ring-out", default="", help="rings workload: write the per-image table here (JSON)")
+    p.add_argument("--frame-steps", type=int, default=8, help="view workload: RK4 steps per frame")
+    p.add_argument("--frame-out", default="", help="view workload: write one frame here (PGM)")
     return p.parse_args()
 
 
@@ -365,8 +369,9 @@ def run_rings(args):
     from paper_1303_5057_gb300 import inputs as I
     wl = I.ring_sweep(args.ring_nr, args.ring_nth)
     ims = wl.images
-    opt = gray.Options(precision=gray.FP32_KAHAN_SEL64, step_rule=gray.STEP_EQ2, h_min=1e-9, max_steps=100000,
-                       r_sw=args.r_sw, block=args.block, blocks_per_sm=args.blocks_per_sm, refill=args.refill)
+    opt = gray.Options(precision=gray.PRECISIONS[args.precision], step_rule=gray.STEP_EQ2, h_min=1e-9,
+                       max_steps=100000, r_sw=args.r_sw, block=args.block, blocks_per_sm=args.blocks_per_sm,
+                       refill=args.refill)
     tr = gray.Tracer(opt, wl.n_rays)
     rows = sum(im.ny for im in ims)
     order = torch.empty(wl.n_rays, dtype=torch.int32, device="cuda")
@@ -408,7 +413,73 @@ def run_rings(args):
                       "R_mean_range": [float(r["R_mean"].min()), float(r["R_mean"].max())],
                       "A_max": float(r["A"].max()), "D_max": float(r["D"].max()),
                       "wrong_rays": int(r["n_wrong"].sum()), "open_rows": int(r["n_open"].sum()),
-                      "clocks": clk}), flush=True)
+                      "precision": args.precision, "clocks": clk}), flush=True)
+    return 0
+
+
+def run_view(args):
+    """The interactive mode of Sec. 2 (Fig. 1) headless: a plane-parallel grid
+    of photons (1024^2, from r = 1000 M) falls onto an a = 0.999 hole; each
+    frame advances every live photon by frame-steps RK4 steps (gray_trace with
+    a step budget) and draws the live photons as sprites into a 1920 x 1080
+    count image (gray_splat), until none is left."""
+    import torch
+    from paper_1303_5057_gb300 import gray
+    from paper_1303_5057_gb300 import inputs as I
+    im = I.Image(a=0.999, incl=math.radians(60.0), nx=args.side, ny=args.side)
+    opt = gray.Options(precision=gray.PRECISIONS[args.precision], max_steps=10000, r_sw=args.r_sw)
+    tr = gray.Tracer(opt, im.n)
+    cam = gray.Camera(eye=(30.0, -22.0, 16.0), look=(0.0, 0.0, 0.0), up=(0.0, 0.0, 1.0), fov=math.radians(60.0),
+                      sprite=1.0, width=1920, height=1080, status_mask=1 << gray.ACTIVE)
+    count = torch.empty((cam.height, cam.width), dtype=torch.int32, device="cuda")
+    depth = torch.empty((cam.height, cam.width), dtype=torch.float32, device="cuda")
+
+    def run(record):
+        tr.setup([im])
+        torch.cuda.synchronize()
+        frames, steps, ms_frames, ms_splat = 0, 0, [], []
+        saved = False
+        while True:
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record()
+            _, n_active, st = tr.trace(step_budget=args.frame_steps, wait=True)
+            e[1].record()
+            gray.gray_splat(tr.ctx, tr.state, tr.n, cam, count=count, depth=depth)
+            e[2].record()
+            torch.cuda.synchronize()
+            frames += 1
+            steps += st[0]
+            ms_frames.append(e[0].elapsed_time(e[2]))
+            ms_splat.append(e[1].elapsed_time(e[2]))
+            if record and args.frame_out and not saved and frames == 24:
+                img = count.cpu().numpy().view(np.uint32)
+                g = np.clip(255.0 * np.log1p(img) / max(1.0, np.log1p(img.max())), 0, 255).astype(np.uint8)
+                with open(args.frame_out, "wb") as f:
+                    f.write(b"P5 %d %d 255\n" % (cam.width, cam.height))
+                    f.write(g.tobytes())
+                saved = True
+            if n_active == 0:
+                return frames, steps, ms_frames, ms_splat
+    run(False)
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    launches0 = gray.gray_launch_count()
+    t0 = time.perf_counter()
+    frames, steps, ms_frames, ms_splat = run(True)
+    wall = time.perf_counter() - t0
+    launches = gray.gray_launch_count() - launches0
+    clocks = clk.stop()
+    tr.close()
+    splat_med = statistics.median(ms_splat)
+    # algorithmic bytes of one splat launch: S0 (16 B) of every ray, position
+    # and compensation (32 B) and spin (32 B of the P plane) of each drawn ray
+    print(json.dumps({"workload": "view_a0.999_i60_%dx%d_photons_1920x1080" % (args.side, args.side),
+                      "metric": "frames/s", "unit": "frames/s", "value": frames / (sum(ms_frames) / 1000.0),
+                      "frames": frames, "frame_steps": args.frame_steps, "photons": im.n,
+                      "ms_per_frame_mean": sum(ms_frames) / frames, "ms_per_frame_max": max(ms_frames),
+                      "splat_ms_median": splat_med, "photon_steps_per_s": steps / (sum(ms_frames) / 1000.0),
+                      "wall_s": wall, "gpu_launches": launches, "precision": args.precision, "clocks": clocks}),
+          flush=True)
     return 0
 
 
@@ -416,6 +487,8 @@ def run_rings(args):
 
 def main():
     args = parse_args()
+    if args.precision is None:
+        args.precision = "fp32_kahan" if args.workload == "rings" else "fp32_kahan_sel64"
     if args.impl == "reference":
         return run_reference(args)
     if args.workload != "kerr1024":
@@ -425,7 +498,8 @@ def main():
         build.build()
         gray.lib()
         return {"schwarzschild64": run_schwarzschild64, "mixed": run_mixed, "sweep": run_sweep,
-                "serve": run_serve, "projection": run_projection, "rings": run_rings}[args.workload](args)
+                "serve": run_serve, "projection": run_projection, "rings": run_rings,
+                "view": run_view}[args.workload](args)
 
     import torch
 

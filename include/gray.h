@@ -311,6 +311,51 @@ int gray_ring(gray_ctx *ctx, const void *state_dev, size_t state_bytes, int64_t 
               gray_ring_info *out_dev, size_t out_bytes, double *boundary_dev, size_t boundary_bytes,
               void *stream);
 
+/* ---- headless view of live photons (gray_splat) --------------------------
+ * GRay's interactive mode (Sec. 2, Fig. 1) draws the photons of the device
+ * buffer while they are being integrated: a shader maps their Boyer-Lindquist
+ * positions to Cartesian space and draws them as point sprites into an OpenGL
+ * frame buffer.  gray_splat does the same arithmetic into plain device images
+ * (no graphics API): position (r, theta, phi) -> x = sqrt(r^2 + a^2) sin(theta)
+ * cos(phi), y = sqrt(r^2 + a^2) sin(theta) sin(phi), z = r cos(theta) (the
+ * Cartesian coordinates in which Boyer-Lindquist ones are oblate spheroidal)
+ * -> camera -> sprite.
+ *
+ * Camera: forward f = (look - eye)/|look - eye|, right s = f x up/|f x up|,
+ * true up u = s x f; a point at d = P - eye has camera coordinates
+ * (d.s, d.u, d.f) and is drawn only when d.f > 0.  Perspective (fov > 0, the
+ * vertical field of view): k = (height/2)/tan(fov/2), image position
+ * (width/2 + k x/z, height/2 - k y/z) pixels, row 0 at the top; orthographic
+ * (fov = 0): k = (height/2)/half_height, (width/2 + k x, height/2 - k y).
+ * Sprite: every pixel whose centre lies within `sprite` pixels of the image
+ * position gets one count and the depth d.f if smaller than the pixel's;
+ * sprite = 0 draws the one pixel containing the position.  Integer counts and
+ * a minimum make the images independent of drawing order (bitwise
+ * reproducible).  A ray is drawn when bit (1 << status) of status_mask is set:
+ * an ACTIVE ray at its current position, a finished ray at its final point on
+ * the stop surface.  FP64 buffers are drawn in double, FP32 buffers in single
+ * precision from the compensated position. */
+typedef struct gray_camera {
+    double eye[3], look[3], up[3]; /* Cartesian, units of M */
+    double fov;                    /* vertical field of view, radians, in [0, pi); 0 = orthographic */
+    double half_height;            /* orthographic: half the image height in M, > 0 */
+    double sprite;                 /* sprite radius in pixels, 0 <= sprite <= 64 */
+    int32_t width, height;         /* image size in pixels, >= 1, width * height < 2^31 */
+    int32_t status_mask;           /* draw rays with status s when bit (1 << s) is set */
+    int32_t clear;                 /* nonzero: zero the counts and set the depths to +inf first */
+} gray_camera;
+
+/* Draw rays first_ray .. first_ray + n - 1 of the buffer into count_dev
+ * (uint32, width x height, row-major, row 0 at the top) and, if not NULL,
+ * depth_dev (float, same shape; +inf where nothing was drawn).  image_bytes
+ * is the size of each of the two images (>= 4 width height).  Without `clear`
+ * the call adds to the images.
+ * Errors: GRAY_EINVAL (bad camera, NULL count image, short images, range
+ * outside the buffer), GRAY_ECUDA. */
+int gray_splat(gray_ctx *ctx, const void *state_dev, size_t state_bytes, int64_t n_state,
+               int64_t first_ray, int64_t n, const gray_camera *camera_host,
+               uint32_t *count_dev, float *depth_dev, size_t image_bytes, void *stream);
+
 /* Maximum number of images one gray_setup_noalloc call accepts. */
 #define GRAY_NOALLOC_MAX_IMAGES 4096
 

@@ -1394,6 +1394,123 @@ __global__ void ring_final_kernel(const RingDev *imgs, int n_images, const doubl
 }
 
 // --------------------------------------------------------------------------
+// Headless view: Boyer-Lindquist -> Cartesian -> camera -> point sprites
+// (the interactive mode of Sec. 2, Fig. 1, without a graphics API)
+// --------------------------------------------------------------------------
+
+struct CamDev {
+    double e[3], s[3], u[3], f[3]; // eye and the camera's right, up, forward unit vectors
+    double k, cx, cy;              // pixels per unit (per unit of x/z in perspective), image centre
+    double sprite;
+    int width, height, ortho, mask;
+};
+
+__global__ void fill_kernel(unsigned *p, int64_t n, unsigned value)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        p[i] = value;
+}
+
+// Deposit one sprite at image position (x, y) with depth z.
+template <typename T>
+__device__ void deposit(const CamDev &c, T x, T y, T z, unsigned *count, float *depth)
+{
+    const T rad = (T)c.sprite;
+    int i0, i1, j0, j1;
+    if (rad <= T(0)) {
+        i0 = i1 = (int)floor(x);
+        j0 = j1 = (int)floor(y);
+    } else {
+        i0 = (int)ceil(x - rad - T(0.5));
+        i1 = (int)floor(x + rad - T(0.5));
+        j0 = (int)ceil(y - rad - T(0.5));
+        j1 = (int)floor(y + rad - T(0.5));
+    }
+    i0 = max(i0, 0);
+    j0 = max(j0, 0);
+    i1 = min(i1, c.width - 1);
+    j1 = min(j1, c.height - 1);
+    const int zbits = __float_as_int((float)z);
+    for (int j = j0; j <= j1; ++j)
+        for (int i = i0; i <= i1; ++i) {
+            if (rad > T(0)) {
+                const T dx = (T)i + T(0.5) - x, dy = (T)j + T(0.5) - y;
+                if (!(dx * dx + dy * dy <= rad * rad))
+                    continue;
+            }
+            const int64_t q = (int64_t)j * c.width + i;
+            atomicAdd(count + q, 1u);
+            if (depth)
+                atomicMin((int *)depth + q, zbits); // positive floats order as their bits
+        }
+}
+
+// One thread per ray: position (current state if active, final point if
+// finished) -> Cartesian -> camera -> sprite, in T (double for FP64 buffers).
+template <typename T>
+__global__ void splat_kernel(StateView v, int prec, int64_t first, int64_t n, CamDev c, unsigned *count, float *depth)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n)
+        return;
+    const int64_t i = first + j;
+    const int st = v.S0[i].x;
+    if (st < 0 || st > 30 || !((c.mask >> st) & 1))
+        return;
+    T r, th, ph;
+    if (prec == GRAY_FP64) {
+        const d4 X = st == GRAY_RAY_ACTIVE ? ld_d4(v.X, i) : ld_d4(v.F, i);
+        r = (T)X.y;
+        th = (T)X.z;
+        ph = (T)X.w;
+    } else if (st != GRAY_RAY_ACTIVE) {
+        const float4 F = ld_f4(v.F, i);
+        r = (T)F.y;
+        th = (T)F.z;
+        ph = (T)F.w;
+    } else if (prec == GRAY_FP32_KAHAN_SEL64 && (v.S1[i].w & FLAG_DOUBLE_REPR)) {
+        const double2 q0 = ((const double2 *)v.X)[i], q1 = ((const double2 *)v.K)[i];
+        r = (T)q0.y;
+        th = (T)q1.x;
+        ph = (T)q1.y;
+    } else {
+        const float4 X = ld_f4(v.X, i);
+        float4 C = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (prec != GRAY_FP32)
+            C = ld_f4(v.CX, i);
+        r = (T)X.y - (T)C.y;
+        th = (T)X.z - (T)C.z;
+        ph = (T)X.w - (T)C.w;
+    }
+    const T a = (T)ld_d4(v.P, i).x;
+    T sth, cth, sph, cph;
+    fsincos(th, &sth, &cth);
+    fsincos(ph, &sph, &cph);
+    const T rho = sqrt(r * r + a * a);
+    const T dx = rho * sth * cph - (T)c.e[0], dy = rho * sth * sph - (T)c.e[1], dz = r * cth - (T)c.e[2];
+    const T x = dx * (T)c.s[0] + dy * (T)c.s[1] + dz * (T)c.s[2];
+    const T y = dx * (T)c.u[0] + dy * (T)c.u[1] + dz * (T)c.u[2];
+    const T z = dx * (T)c.f[0] + dy * (T)c.f[1] + dz * (T)c.f[2];
+    if (!(z > T(0)))
+        return;
+    T px, py;
+    if (c.ortho) {
+        px = (T)c.cx + (T)c.k * x;
+        py = (T)c.cy - (T)c.k * y;
+    } else {
+        px = (T)c.cx + (T)c.k * x / z;
+        py = (T)c.cy - (T)c.k * y / z;
+    }
+    // off-image positions whose sprite cannot reach the image are skipped
+    // before any conversion to int
+    const T reach = (T)c.sprite + T(1);
+    if (!(px > -reach && px < (T)c.width + reach && py > -reach && py < (T)c.height + reach))
+        return;
+    deposit<T>(c, px, py, z, count, depth);
+}
+
+// --------------------------------------------------------------------------
 // Unit evaluations for parity tests
 // --------------------------------------------------------------------------
 
@@ -2140,6 +2257,79 @@ int gray_ring(gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_st
     if (rc)
         return rc;
     return cuda_err(e);
+}
+
+int gray_splat(gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_state, int64_t first_ray, int64_t n,
+               const gray_camera *cam, uint32_t *count, float *depth, size_t image_bytes, void *stream)
+{
+    int rc = check_state(ctx, state, state_bytes, n_state);
+    if (rc)
+        return rc;
+    if (!cam || !count || first_ray < 0 || n < 0 || first_ray + n > n_state)
+        return GRAY_EINVAL;
+    if (!finite_all({cam->eye[0], cam->eye[1], cam->eye[2], cam->look[0], cam->look[1], cam->look[2], cam->up[0],
+                     cam->up[1], cam->up[2], cam->fov, cam->half_height, cam->sprite}))
+        return GRAY_EINVAL;
+    if (cam->width < 1 || cam->height < 1 || (int64_t)cam->width * cam->height >= ((int64_t)1 << 31))
+        return GRAY_EINVAL;
+    if (!(cam->fov >= 0.0) || !(cam->fov < 3.14159265358979323846) || !(cam->sprite >= 0.0) ||
+        !(cam->sprite <= 64.0) || (cam->fov == 0.0 && !(cam->half_height > 0.0)))
+        return GRAY_EINVAL;
+    const int64_t npix = (int64_t)cam->width * cam->height;
+    if (image_bytes < sizeof(uint32_t) * (size_t)npix)
+        return GRAY_EINVAL;
+    CamDev c;
+    double f[3], s3[3], u[3];
+    for (int m = 0; m < 3; ++m)
+        f[m] = cam->look[m] - cam->eye[m];
+    const double fl = std::sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    if (!(fl > 0.0))
+        return GRAY_EINVAL;
+    for (int m = 0; m < 3; ++m)
+        f[m] /= fl;
+    s3[0] = f[1] * cam->up[2] - f[2] * cam->up[1];
+    s3[1] = f[2] * cam->up[0] - f[0] * cam->up[2];
+    s3[2] = f[0] * cam->up[1] - f[1] * cam->up[0];
+    const double sl = std::sqrt(s3[0] * s3[0] + s3[1] * s3[1] + s3[2] * s3[2]);
+    if (!(sl > 1e-12))
+        return GRAY_EINVAL; // up parallel to the viewing direction
+    for (int m = 0; m < 3; ++m)
+        s3[m] /= sl;
+    u[0] = s3[1] * f[2] - s3[2] * f[1];
+    u[1] = s3[2] * f[0] - s3[0] * f[2];
+    u[2] = s3[0] * f[1] - s3[1] * f[0];
+    for (int m = 0; m < 3; ++m) {
+        c.e[m] = cam->eye[m];
+        c.s[m] = s3[m];
+        c.u[m] = u[m];
+        c.f[m] = f[m];
+    }
+    c.ortho = cam->fov == 0.0;
+    c.k = c.ortho ? 0.5 * cam->height / cam->half_height : 0.5 * cam->height / std::tan(0.5 * cam->fov);
+    c.cx = 0.5 * cam->width;
+    c.cy = 0.5 * cam->height;
+    c.sprite = cam->sprite;
+    c.width = cam->width;
+    c.height = cam->height;
+    c.mask = cam->status_mask;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cam->clear) {
+        if (cudaMemsetAsync(count, 0, sizeof(uint32_t) * (size_t)npix, st) != cudaSuccess)
+            return GRAY_ECUDA;
+        if (depth) {
+            fill_kernel<<<grid_for(npix, 256), 256, 0, st>>>((unsigned *)depth, npix, 0x7f800000u);
+            if ((rc = check_launch()))
+                return rc;
+        }
+    }
+    if (n == 0)
+        return GRAY_OK;
+    const StateView v = make_view((void *)state, n_state, ctx->opt.precision);
+    if (ctx->opt.precision == GRAY_FP64)
+        splat_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(v, ctx->opt.precision, first_ray, n, c, count, depth);
+    else
+        splat_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(v, ctx->opt.precision, first_ray, n, c, count, depth);
+    return check_launch();
 }
 
 int gray_eval(int32_t what, int32_t precision, const double *in, int64_t n, double *out, void *stream)

@@ -54,6 +54,35 @@ class _Image(C.Structure):
                 ("beta0", C.c_double), ("beta1", C.c_double), ("grid", C.c_int32), ("reserved", C.c_int32)]
 
 
+class _Camera(C.Structure):
+    _fields_ = [("eye", C.c_double * 3), ("look", C.c_double * 3), ("up", C.c_double * 3), ("fov", C.c_double),
+                ("half_height", C.c_double), ("sprite", C.c_double), ("width", C.c_int32), ("height", C.c_int32),
+                ("status_mask", C.c_int32), ("clear", C.c_int32)]
+
+
+@dataclass
+class Camera:
+    """Camera of gray_splat (see include/gray.h): eye, look-at point and up
+    vector in Cartesian units of M; vertical field of view in radians (0 =
+    orthographic with the given half height); sprite radius in pixels;
+    status_mask selects the rays drawn by status (bit 1 << status)."""
+    eye: tuple = (60.0, 0.0, 20.0)
+    look: tuple = (0.0, 0.0, 0.0)
+    up: tuple = (0.0, 0.0, 1.0)
+    fov: float = 0.7
+    half_height: float = 10.0
+    sprite: float = 0.0
+    width: int = 640
+    height: int = 480
+    status_mask: int = 1
+    clear: int = 1
+
+    def _c(self):
+        d3 = C.c_double * 3
+        return _Camera(d3(*self.eye), d3(*self.look), d3(*self.up), float(self.fov), float(self.half_height),
+                       float(self.sprite), int(self.width), int(self.height), int(self.status_mask), int(self.clear))
+
+
 SHADOW_DTYPE = np.dtype([("n_captured", "<i8"), ("n_escaped", "<i8"), ("n_other", "<i8"),
                          ("area", "<f8"), ("radius", "<f8"), ("alpha_c", "<f8"), ("beta_c", "<f8")])
 PIXEL64_DTYPE = np.dtype([("r", "<f8"), ("theta", "<f8"), ("phi", "<f8"), ("status", "<i4"), ("steps", "<i4")])
@@ -126,6 +155,8 @@ def lib():
     L.gray_shadow.restype = C.c_int
     L.gray_ring.argtypes = [vp, vp, sz, i64, i64, C.POINTER(_Image), i32, vp, sz, vp, sz, vp]
     L.gray_ring.restype = C.c_int
+    L.gray_splat.argtypes = [vp, vp, sz, i64, i64, i64, C.POINTER(_Camera), vp, vp, sz, vp]
+    L.gray_splat.restype = C.c_int
     L.gray_eval.argtypes = [i32, i32, vp, i64, vp, vp]
     L.gray_eval.restype = C.c_int
     L.gray_set_timing.argtypes = [vp, i32]
@@ -333,6 +364,25 @@ def gray_ring(ctx, state, n_state, images, first_ray=0, out=None, boundary=None,
                            int(first_ray), arr, len(images), _ptr(out), out.numel() * out.element_size(),
                            bp, bb, _stream(stream)), "gray_ring")
     return out
+
+
+def gray_splat(ctx, state, n_state, camera, count=None, depth=None, first_ray=0, n=None, stream=None):
+    """Draw rays first_ray .. first_ray + n - 1 into count (uint32 as int32
+    CUDA tensor of height x width) and optionally depth (float32, same
+    shape).  Returns (count, depth)."""
+    import torch
+    if n is None:
+        n = n_state - first_ray
+    if count is None:
+        count = torch.empty((camera.height, camera.width), dtype=torch.int32, device=state.device)
+    nbytes = count.numel() * count.element_size()
+    if depth is not None:
+        assert depth.numel() * depth.element_size() == nbytes
+    cam = camera._c()
+    _check(lib().gray_splat(ctx, _ptr(state), state.numel() * state.element_size(), int(n_state), int(first_ray),
+                            int(n), C.byref(cam), _ptr(count), _ptr(depth) if depth is not None else None, nbytes,
+                            _stream(stream)), "gray_splat")
+    return count, depth
 
 
 def gray_eval(what, precision, inp, stream=None):

@@ -1,0 +1,172 @@
+"""GPU parity of the headless view (gray_splat; the interactive mode of Sec. 2,
+Fig. 1, without a graphics API) against the splat oracle (oracle/splat.py).
+
+The oracle traces the same rays itself (FP64, same number of steps) and draws
+its own positions.  Bars: FP64 buffers give the oracle's count image exactly
+(pixels decided by a position within 1e-9 px of a pixel edge or of a sprite's
+rim excepted; none occur in these cases) and its depths to 1e-6; compensated
+FP32 buffers differ from it in under 1 % of the drawn pixels.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import parity as P
+from oracle import splat as S
+from paper_1303_5057_gb300 import gray
+from paper_1303_5057_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+IM = I.Image(a=0.999, incl=math.radians(60.0), nx=48, ny=40, r_obs=100.0)
+CAM = dict(eye=(40.0, -30.0, 25.0), look=(0.0, 0.0, 0.0), up=(0.0, 0.0, 1.0), fov=math.radians(50.0),
+           half_height=10.0, width=320, height=240, sprite=1.5)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1303_5057_gb300 import build
+    build.build()
+    gray.lib()
+    oracle.lib()
+    torch.cuda.init()
+
+
+def _rays():
+    return oracle.image_rays(IM.a, IM.incl, IM.r_obs, IM.nx, IM.ny, IM.alpha0, IM.alpha1, IM.beta0, IM.beta1)
+
+
+def _oracle(max_steps, **kw):
+    return oracle.trace_many(_rays(), oracle.Options(max_steps=max_steps, **kw))
+
+
+def _ambiguous(cam, px, py, vis):
+    """Points whose pixels a 1e-9 px change could alter."""
+    rad, amb = cam["sprite"], 0
+    for x, y, ok in zip(px, py, vis):
+        if not ok:
+            continue
+        if rad <= 0:
+            amb += min(abs(x - round(x)), abs(y - round(y))) < 1e-9
+            continue
+        for j in range(math.floor(y - rad) - 1, math.ceil(y + rad) + 2):
+            for i in range(math.floor(x - rad) - 1, math.ceil(x + rad) + 2):
+                if abs((i + 0.5 - x) ** 2 + (j + 0.5 - y) ** 2 - rad * rad) < 1e-8:
+                    amb += 1
+    return amb
+
+
+def _gpu(prec, budget, cam, mask, trace=True, **kw):
+    tr = gray.Tracer(gray.Options(precision=prec, r_sw=0.02, **kw), IM.n)
+    tr.setup([IM])
+    if trace:
+        tr.trace(step_budget=budget)
+    rec = tr.records()
+    st = rec[:, 0].astype(int)
+    c = gray.Camera(**cam, status_mask=mask)
+    depth = torch.empty((cam["height"], cam["width"]), dtype=torch.float32, device="cuda")
+    count, depth = gray.gray_splat(tr.ctx, tr.state, tr.n, c, depth=depth)
+    torch.cuda.synchronize()
+    out = count.cpu().numpy().view(np.uint32), depth.cpu().numpy(), st, rec
+    tr.close()
+    return out
+
+
+def test_live_photons_fp64_match_oracle():
+    """Mid-flight (170 steps into the trace: some photons captured, most still
+    in flight) the photons' current positions, sprites of radius 1.5 px."""
+    ref = _oracle(170)
+    live = ref[:, 0] == oracle.STEP_CAP
+    assert 0.3 < live.mean() < 1.0
+    count, depth, st, _ = _gpu(gray.FP64, 170, CAM, 1 << gray.ACTIVE)
+    assert np.array_equal(st == gray.ACTIVE, live)
+    y = ref[live, 8:16]
+    X, Y, Z = S.bl_to_cartesian(IM.a, y[:, 1], y[:, 2], y[:, 3])
+    px, py, z, vis = S.project(CAM, X, Y, Z)
+    c_ref, z_ref = S.splat(CAM, px, py, z, vis)
+    assert _ambiguous(CAM, px, py, vis) == 0
+    assert c_ref.sum() > 1000
+    assert np.array_equal(count, c_ref)
+    hit = c_ref > 0
+    assert np.all(np.isinf(depth[~hit]))
+    assert np.allclose(depth[hit], z_ref[hit], rtol=1e-6)
+
+
+def test_finished_photons_at_their_final_points_fp64():
+    """Traced to the end under Eq. 2 (the paper's rule, no floor): captured
+    photons drawn on the capture surface, escaped ones on the sphere
+    r = r_obs, one pixel each, orthographic."""
+    cam = dict(CAM, eye=(300.0, 40.0, 90.0), fov=0.0, half_height=120.0, sprite=0.0, width=256, height=256)
+    ref = _oracle(100000, step_rule=oracle.STEP_EQ2, h_min=1e-9)
+    count, depth, st, rec = _gpu(gray.FP64, 0, cam, (1 << gray.CAPTURED) | (1 << gray.ESCAPED),
+                                 step_rule=gray.STEP_EQ2, h_min=1e-9)
+    # A ray's FP64 final point may leave the oracle's by more than rounding
+    # (or the ray may end otherwise) only where the method itself is not
+    # faithful: within 0.05 M of the critical curve (chaotic) or where the
+    # oracle's own trajectory does not conserve Carter's constant (Euler
+    # crawl).  Each such ray can change at most two pixels.
+    rays = _rays()
+    far = P.band_mask((rays[:, 0], rays[:, 1]), IM.a, IM.incl)
+    sane = P.oracle_q_drift(oracle, rays, ref) < P.SANE_Q
+    dfin = np.abs(rec[:, 5:8] - ref[:, 5:8]).max(axis=1) / np.maximum(1.0, np.abs(ref[:, 5:8]).max(axis=1))
+    diverged = (st != ref[:, 0].astype(int)) | ~(dfin <= 1e-9)
+    assert not np.any(diverged & far & sane)
+    disagree = int(diverged.sum())
+    assert disagree <= 30
+    done = (ref[:, 0] == oracle.CAPTURED) | (ref[:, 0] == oracle.ESCAPED)
+    f = ref[done, 4:8]
+    X, Y, Z = S.bl_to_cartesian(IM.a, f[:, 1], f[:, 2], f[:, 3])
+    px, py, z, vis = S.project(cam, X, Y, Z)
+    c_ref, z_ref = S.splat(cam, px, py, z, vis)
+    assert _ambiguous(cam, px, py, vis) == 0
+    same = count == c_ref
+    assert int((~same).sum()) <= 2 * disagree
+    both = same & (c_ref > 0)
+    assert both.sum() > 500
+    assert np.allclose(depth[both], z_ref[both], rtol=1e-6)
+
+
+def test_live_photons_fp32_close_to_oracle():
+    ref = _oracle(170)
+    live = ref[:, 0] == oracle.STEP_CAP
+    count, _, st, _ = _gpu(gray.FP32_KAHAN_SEL64, 170, CAM, 1 << gray.ACTIVE)
+    assert np.array_equal(st == gray.ACTIVE, live)
+    y = ref[live, 8:16]
+    X, Y, Z = S.bl_to_cartesian(IM.a, y[:, 1], y[:, 2], y[:, 3])
+    c_ref, _ = S.splat(CAM, *S.project(CAM, X, Y, Z))
+    differ = int((count != c_ref).sum())
+    assert differ <= 0.01 * int((c_ref > 0).sum())
+    assert abs(int(count.sum()) - int(c_ref.sum())) <= 0.01 * int(c_ref.sum())
+
+
+def test_images_accumulate_without_clear_and_set_up_states_draw():
+    tr = gray.Tracer(gray.Options(precision=gray.FP64), IM.n)
+    tr.setup([IM])
+    # looking at the image plane (r_obs = 100 along (sin i, 0, cos i)) from 300 M
+    c1 = gray.Camera(**dict(CAM, eye=(259.8, 0.0, 150.0)), status_mask=1 << gray.ACTIVE)
+    count, _ = gray.gray_splat(tr.ctx, tr.state, tr.n, c1)
+    once = count.cpu().numpy().copy()
+    c1.clear = 0
+    gray.gray_splat(tr.ctx, tr.state, tr.n, c1, count=count)
+    gray.gray_splat(tr.ctx, tr.state, tr.n, c1, count=count, first_ray=5, n=0)
+    twice = count.cpu().numpy()
+    tr.close()
+    assert once.sum() > 0 and np.array_equal(twice, 2 * once)
+
+
+def test_bad_cameras_are_rejected():
+    tr = gray.Tracer(gray.Options(precision=gray.FP64), 16)
+    bad = [dict(up=(-40.0, 30.0, -25.0)), dict(width=0), dict(sprite=65.0), dict(fov=0.0, half_height=0.0),
+           dict(fov=math.pi), dict(look=CAM["eye"])]
+    for b in bad:
+        with pytest.raises(gray.GrayError):
+            gray.gray_splat(tr.ctx, tr.state, tr.n, gray.Camera(**dict(CAM, **b)))
+    with pytest.raises(gray.GrayError):  # range outside the buffer
+        gray.gray_splat(tr.ctx, tr.state, tr.n, gray.Camera(**CAM), first_ray=10, n=10)
+    with pytest.raises(gray.GrayError):  # image too small
+        gray.gray_splat(tr.ctx, tr.state, tr.n, gray.Camera(**CAM),
+                        count=torch.empty((10, 10), dtype=torch.int32, device="cuda"))
+    tr.close()
