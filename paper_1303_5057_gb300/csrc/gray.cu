@@ -55,7 +55,7 @@ __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_
 //   S1 (steps in double, call epoch, steps in that call, flags)  int4
 //   L  hand-off list of ray indices (selective-double mode)  int
 struct Layout {
-    size_t X, K, CX, CK, F, P, PF0, PF1, S0, S1, L, total;
+    size_t X, K, CX, CK, F, P, PF0, PF1, S0, S1, L, R, total;
 };
 
 inline bool is_f64(int prec) { return prec == GRAY_FP64; }
@@ -96,6 +96,12 @@ Layout make_layout(int64_t n, int prec)
     off = align256(off + 16 * un);
     L.L = off;
     off = align256(off + 4 * un);
+    if (prec == GRAY_FP32_KAHAN_SEL64) {
+        L.R = off; // rays the double zone returns to single precision
+        off = align256(off + 4 * un);
+    } else {
+        L.R = 0;
+    }
     L.total = off;
     return L;
 }
@@ -107,6 +113,7 @@ struct StateView {
     int4 *S0;
     int4 *S1;
     int *L;
+    int *R;
 };
 
 StateView make_view(void *base, int64_t n, int prec)
@@ -125,6 +132,7 @@ StateView make_view(void *base, int64_t n, int prec)
     v.S0 = (int4 *)(b + L.S0);
     v.S1 = (int4 *)(b + L.S1);
     v.L = (int *)(b + L.L);
+    v.R = prec == GRAY_FP32_KAHAN_SEL64 ? (int *)(b + L.R) : nullptr;
     return v;
 }
 
@@ -327,9 +335,9 @@ template <typename T, bool KAHAN> __device__ __forceinline__ int remap_eq3(T *y,
 }
 
 __device__ __forceinline__ float sixth(float h) { return h * (1.0f / 6.0f); }
-__device__ __forceinline__ double sixth(double h) { return h / 6.0; }
+__device__ __forceinline__ double sixth(double h) { return h * (1.0 / 6.0); }
 __device__ __forceinline__ float ninth(float h) { return h * (1.0f / 9.0f); }
-__device__ __forceinline__ double ninth(double h) { return h / 9.0; }
+__device__ __forceinline__ double ninth(double h) { return h * (1.0 / 9.0); }
 
 // One step.  Returns the ray's new status; writes fin[4] when it stops.  g
 // holds the geometry of the current point on entry and of the new point on
@@ -447,6 +455,7 @@ struct TraceArgs {
                           // S1.y == epoch means S1.z counts this call's steps
     int one_per_thread; // the paper's launch: thread g takes queue slot g only
     int stop_equator;   // Sec. 3 grid projection: stop at the equatorial plane
+    int zone_return;    // zone pass: a ray climbing out of the zone goes to the return list
     double h_frac, h_min, eps_xi, cap_frac, r_esc_frac, r_sw;
     Workspace *ws;
 };
@@ -753,12 +762,18 @@ __global__ void __launch_bounds__(128) trace64_kernel(TraceArgs A)
 }
 
 // Zone kernel of GRAY_FP32_KAHAN_SEL64: the rays of the hand-off list, in
-// double precision while r < r_demote (= r_promote + r_sw) and in compensated
-// single precision once they climb out, switching back when they fall below
-// r_promote again -- so every handed-off ray finishes here and no further
-// single-precision pass is needed.  The switches are exact one way (hi - lo
-// to double) and a rounding the other way (double to hi, lo).
-__global__ void __launch_bounds__(128, 1) zone_kernel(TraceArgs A)
+// double precision while r < r_demote (= r_promote + r_sw).  RETURN = true
+// (first zone pass): double only; a ray that climbs out is stored as a
+// compensated single pair and appended to the return list R, which the next
+// single-precision pass drains at full occupancy (this kernel holds no
+// single-precision state and fits three blocks per SM).  RETURN = false (last
+// zone pass): a ray that climbs out continues in compensated single precision
+// here, switching back below r_promote, so every handed-off ray finishes.
+// The switches are exact one way (hi - lo to double) and a rounding the other
+// way (double to hi, lo), the same in both forms, so a ray's arithmetic does
+// not depend on which pass runs it.
+template <bool RETURN>
+__global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -821,8 +836,9 @@ __global__ void __launch_bounds__(128, 1) zone_kernel(TraceArgs A)
                         used = (s1.y == epoch) ? s1.z : 0;
                         const d4 p = ld_d4(v.P, my);
                         Hd = make_hole(p.x, p.y, p.z, A.cap_frac, A.r_esc_frac, A.r_sw);
-                        Hf = make_hole_f(v.PF0[my], v.PF1[my], (float)A.cap_frac, (float)A.r_esc_frac,
-                                         (float)A.r_sw);
+                        if (!RETURN)
+                            Hf = make_hole_f(v.PF0[my], v.PF1[my], (float)A.cap_frac, (float)A.r_esc_frac,
+                                             (float)A.r_sw);
                         r_demote = Hd.r_promote + A.r_sw;
                         if (s1.w & FLAG_DOUBLE_REPR) {
                             // exact double state parked in the four single planes
@@ -849,76 +865,100 @@ __global__ void __launch_bounds__(128, 1) zone_kernel(TraceArgs A)
             break;
 
         for (int k = 0; k < A.refill; ++k) {
-            if (!has)
-                continue;
-            int status = GRAY_RAY_ACTIVE;
-            bool yield = false;
-            if (steps >= A.max_steps) {
-                status = GRAY_RAY_STEP_CAP;
-                for (int m = 0; m < 4; ++m)
-                    find[m] = dbl ? yd[m] : (double)yf[m] - (double)cf[m];
-            } else if (A.budget > 0 && used >= A.budget) {
-                yield = true;
-            } else if (dbl && yd[1] >= r_demote) {
-                // climb out of the zone: back to a compensated single pair
-#pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    yf[m] = (float)yd[m];
-                    cf[m] = (float)((double)yf[m] - yd[m]);
-                }
-                gf = geometry(Hf, yf[1], yf[2], -cf[1], -cf[2]);
-                dbl = false;
-                continue;
-            } else if (!dbl && yf[1] - cf[1] < Hf.r_promote) {
-#pragma unroll
-                for (int m = 0; m < 8; ++m)
-                    yd[m] = (double)yf[m] - (double)cf[m];
-                gd = geometry(Hd, yd[1], yd[2]);
-                dbl = true;
-                continue;
-            } else {
-                const int e0 = euler;
-                if (dbl) {
-                    status = step_once<double, false>(Hd, Od, yd, cz, gd, find, euler, remaps);
-                    ++n64;
-                    ++tot_fp64;
-                } else {
-                    status = step_once<float, true>(Hf, Of, yf, cf, gf, finf, euler, remaps);
+            bool ret = false; // this lane's ray climbed out and goes to the return list
+            if (has) {
+                int status = GRAY_RAY_ACTIVE;
+                bool yield = false, stepped = true;
+                if (steps >= A.max_steps) {
+                    status = GRAY_RAY_STEP_CAP;
                     for (int m = 0; m < 4; ++m)
-                        find[m] = finf[m];
-                }
-                tot_euler += (unsigned long long)(euler - e0);
-                ++steps;
-                ++used;
-                ++tot_steps;
-            }
-            if (status == GRAY_RAY_ACTIVE && !yield)
-                continue;
-            int flags = 0;
-            if (yield && dbl) {
-                // park the exact double state; the ray resumes in double
-                ((double2 *)v.X)[id] = make_double2(yd[0], yd[1]);
-                ((double2 *)v.K)[id] = make_double2(yd[2], yd[3]);
-                ((double2 *)v.CX)[id] = make_double2(yd[4], yd[5]);
-                ((double2 *)v.CK)[id] = make_double2(yd[6], yd[7]);
-                flags = FLAG_DOUBLE_MODE | FLAG_DOUBLE_REPR;
-            } else {
-                float hi[8], lo[8];
+                        find[m] = dbl ? yd[m] : (double)yf[m] - (double)cf[m];
+                } else if (A.budget > 0 && used >= A.budget) {
+                    yield = true;
+                } else if (dbl && yd[1] >= r_demote) {
+                    // climb out of the zone: back to a compensated single pair
+                    stepped = false;
+                    if (RETURN) {
+                        float hi[8], lo[8];
 #pragma unroll
-                for (int m = 0; m < 8; ++m) {
-                    hi[m] = dbl ? (float)yd[m] : yf[m];
-                    lo[m] = dbl ? (float)((double)hi[m] - yd[m]) : cf[m];
+                        for (int m = 0; m < 8; ++m) {
+                            hi[m] = (float)yd[m];
+                            lo[m] = (float)((double)hi[m] - yd[m]);
+                        }
+                        st_f4(v.X, id, hi[0], hi[1], hi[2], hi[3]);
+                        st_f4(v.K, id, hi[4], hi[5], hi[6], hi[7]);
+                        st_f4(v.CX, id, lo[0], lo[1], lo[2], lo[3]);
+                        st_f4(v.CK, id, lo[4], lo[5], lo[6], lo[7]);
+                        v.S0[id] = make_int4(GRAY_RAY_ACTIVE, steps, euler, remaps);
+                        v.S1[id] = make_int4(n64, epoch, used, 0);
+                        has = false;
+                        ret = true;
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) {
+                            yf[m] = (float)yd[m];
+                            cf[m] = (float)((double)yf[m] - yd[m]);
+                        }
+                        gf = geometry(Hf, yf[1], yf[2], -cf[1], -cf[2]);
+                        dbl = false;
+                    }
+                } else if (!RETURN && !dbl && yf[1] - cf[1] < Hf.r_promote) {
+                    stepped = false;
+#pragma unroll
+                    for (int m = 0; m < 8; ++m)
+                        yd[m] = (double)yf[m] - (double)cf[m];
+                    gd = geometry(Hd, yd[1], yd[2]);
+                    dbl = true;
+                } else {
+                    const int e0 = euler;
+                    if (RETURN || dbl) {
+                        status = step_once<double, false>(Hd, Od, yd, cz, gd, find, euler, remaps);
+                        ++n64;
+                        ++tot_fp64;
+                    } else {
+                        status = step_once<float, true>(Hf, Of, yf, cf, gf, finf, euler, remaps);
+                        for (int m = 0; m < 4; ++m)
+                            find[m] = finf[m];
+                    }
+                    tot_euler += (unsigned long long)(euler - e0);
+                    ++steps;
+                    ++used;
+                    ++tot_steps;
                 }
-                st_f4(v.X, id, hi[0], hi[1], hi[2], hi[3]);
-                st_f4(v.K, id, hi[4], hi[5], hi[6], hi[7]);
-                st_f4(v.CX, id, lo[0], lo[1], lo[2], lo[3]);
-                st_f4(v.CK, id, lo[4], lo[5], lo[6], lo[7]);
-                if (status != GRAY_RAY_ACTIVE)
-                    st_f4(v.F, id, (float)find[0], (float)find[1], (float)find[2], (float)find[3]);
+                if (stepped && (status != GRAY_RAY_ACTIVE || yield)) {
+                    int flags = 0;
+                    if (yield && dbl) {
+                        // park the exact double state; the ray resumes in double
+                        ((double2 *)v.X)[id] = make_double2(yd[0], yd[1]);
+                        ((double2 *)v.K)[id] = make_double2(yd[2], yd[3]);
+                        ((double2 *)v.CX)[id] = make_double2(yd[4], yd[5]);
+                        ((double2 *)v.CK)[id] = make_double2(yd[6], yd[7]);
+                        flags = FLAG_DOUBLE_MODE | FLAG_DOUBLE_REPR;
+                    } else {
+                        float hi[8], lo[8];
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) {
+                            hi[m] = dbl ? (float)yd[m] : yf[m];
+                            lo[m] = dbl ? (float)((double)hi[m] - yd[m]) : cf[m];
+                        }
+                        st_f4(v.X, id, hi[0], hi[1], hi[2], hi[3]);
+                        st_f4(v.K, id, hi[4], hi[5], hi[6], hi[7]);
+                        st_f4(v.CX, id, lo[0], lo[1], lo[2], lo[3]);
+                        st_f4(v.CK, id, lo[4], lo[5], lo[6], lo[7]);
+                        if (status != GRAY_RAY_ACTIVE)
+                            st_f4(v.F, id, (float)find[0], (float)find[1], (float)find[2], (float)find[3]);
+                    }
+                    v.S0[id] = make_int4(status, steps, euler, remaps);
+                    v.S1[id] = make_int4(n64, epoch, used, flags);
+                    has = false;
+                }
             }
-            v.S0[id] = make_int4(status, steps, euler, remaps);
-            v.S1[id] = make_int4(n64, epoch, used, flags);
-            has = false;
+            if (RETURN) {
+                int rank;
+                const unsigned long long rb = warp_count(&A.ws->demoted, ret, lane, &rank);
+                if (ret)
+                    v.R[rb + rank] = (int)id;
+            }
         }
     }
     warp_stats<double>(A, lane, tot_steps, tot_euler, tot_fp64, true);
@@ -1549,6 +1589,8 @@ template <typename T> __global__ void eval_kernel(int what, const double *in, in
         fsincos((T)in[i], &sv, &cv);
         out[2 * i] = (double)sv;
         out[2 * i + 1] = (double)cv;
+    } else if (what == GRAY_EVAL_RECIP) {
+        out[i] = (double)recip((T)in[i]);
     } else if (what == GRAY_EVAL_XI) {
         const double *q = in + 10 * i;
         const Hole<T> H = cast_hole<T>(make_hole(q[1], q[0], 1.0, 1.0, 1.0, 0.0));
@@ -1851,6 +1893,7 @@ TraceArgs make_trace_args(gray_ctx *ctx, void *state, int64_t n_state, int64_t s
     A.ws = ctx->ws;
     A.one_per_thread = o.launch == GRAY_LAUNCH_ONE_PER_THREAD;
     A.stop_equator = o.stop_equator;
+    A.zone_return = 0;
     return A;
 }
 
@@ -1948,19 +1991,38 @@ int gray_trace(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, 
         if (ctx->timing)
             cudaEventRecord(ctx->ev[1], s);
         if (ctx->opt.precision == GRAY_FP32_KAHAN_SEL64) {
-            // the zone kernel takes the rays the single pass handed off (the
-            // count stays on the device)
-            if (cudaMemsetAsync(&ctx->ws->head, 0, sizeof(unsigned long long), s) != cudaSuccess)
-                return GRAY_ECUDA;
+            // 1. the rays the single pass handed off, in double; those that
+            //    climb out go to the return list (all counts stay on the
+            //    device); 2. a single-precision pass over the return list;
+            // 3. its hand-offs, in double with a single-precision tail.
             const int block = ctx->opt.block > 0 ? ctx->opt.block : 128;
             // rays spend only a few steps in the zone: refill lanes often
             TraceArgs Z = A;
-            Z.refill = 2;
+            Z.refill = 1;
+            Z.zone_return = 1;
+            TraceArgs B = A;
+            B.order = A.v.R;
+            B.n_queue_dev = &ctx->ws->demoted;
             if (ctx->timing) {
                 cudaEventRecord(ctx->ev[2], s);
                 ctx->ev_used[1] = true;
             }
-            zone_kernel<<<persistent_grid(ctx, (const void *)zone_kernel, block, work), block, 0, s>>>(Z);
+            if (cudaMemsetAsync(&ctx->ws->head, 0, sizeof(unsigned long long), s) != cudaSuccess)
+                return GRAY_ECUDA;
+            zone_kernel<true><<<persistent_grid(ctx, (const void *)zone_kernel<true>, block, work), block, 0, s>>>(Z);
+            if ((rc = check_launch()))
+                return rc;
+            // the hand-off list is consumed: pass B appends to it from 0
+            if (cudaMemsetAsync(&ctx->ws->head, 0, sizeof(unsigned long long), s) != cudaSuccess ||
+                cudaMemsetAsync(&ctx->ws->handoff, 0, sizeof(unsigned long long), s) != cudaSuccess)
+                return GRAY_ECUDA;
+            if ((rc = launch_pass(ctx, B, work, s)))
+                return rc;
+            if (cudaMemsetAsync(&ctx->ws->head, 0, sizeof(unsigned long long), s) != cudaSuccess)
+                return GRAY_ECUDA;
+            Z.zone_return = 0;
+            zone_kernel<false>
+                <<<persistent_grid(ctx, (const void *)zone_kernel<false>, block, work), block, 0, s>>>(Z);
             if ((rc = check_launch()))
                 return rc;
             if (ctx->timing)
@@ -2334,7 +2396,7 @@ int gray_splat(gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_s
 
 int gray_eval(int32_t what, int32_t precision, const double *in, int64_t n, double *out, void *stream)
 {
-    if (what < GRAY_EVAL_CHRISTOFFEL || what > GRAY_EVAL_SINCOS || n < 0)
+    if (what < GRAY_EVAL_CHRISTOFFEL || what > GRAY_EVAL_RECIP || n < 0)
         return GRAY_EINVAL;
     if (precision != GRAY_FP64 && precision != GRAY_FP32)
         return GRAY_EINVAL;

@@ -234,8 +234,10 @@ __device__ inline void christoffel_closed_form(const Hole<T> &H, T r, T th, T *G
 #undef GSET
 }
 
-// Reciprocal.  Single precision: the hardware approximation refined by one
-// Newton-Raphson step r <- r (2 - x r) (about 1 ulp); double: a true divide.
+// Reciprocal: the hardware approximation refined by Newton-Raphson steps
+// r <- r + r (1 - x r): one in single precision, two in double (each step
+// squares the relative error; about 1 ulp at the end).  On GB300 a double
+// divide is a long sequence on the narrow FP64 pipe.
 __device__ __forceinline__ float recip(float x)
 {
     float r;
@@ -243,7 +245,15 @@ __device__ __forceinline__ float recip(float x)
     const float e = fmaf(-x, r, 1.0f);
     return fmaf(r, e, r);
 }
-__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ double recip(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
 
 // Geometry of one point (r, theta): the quantities every right-hand side and
 // the Eq. 4 monitor need.  Single precision takes the three reciprocals from
@@ -434,9 +444,9 @@ template <typename T> __device__ __forceinline__ T step_size(const Hole<T> &H, c
         else
             h = fmin(O.h_frac * r, guard);
     } else {
-        guard = (r - H.r_h) / (T(2) * fabs(kr));
+        guard = (r - H.r_h) * (T(0.5) * recip(fabs(kr)));
         if (O.step_rule == 1)
-            h = fmin(O.h_frac / (fabs(kr / r) + fabs(y[6]) + fabs(y[7])), guard);
+            h = fmin(O.h_frac * recip(fabs(kr) * recip(r) + fabs(y[6]) + fabs(y[7])), guard);
         else
             h = fmin(O.h_frac * r, guard);
     }
@@ -455,32 +465,41 @@ template <typename T> __device__ __forceinline__ T hermite(T x0, T v0, T x1, T v
     return h00 * x0 + h10 * h * v0 + h01 * x1 + h11 * h * v1;
 }
 
-template <typename T> struct BisectIters;
-template <> struct BisectIters<float> { static constexpr int value = 30; };
-template <> struct BisectIters<double> { static constexpr int value = 60; };
-
 // Fraction s of the last step at which coordinate m (1: r, 2: theta) of the
-// Hermite interpolant reaches `target`.  Double: bisection (60 halvings, as
-// the oracle).  Single: Newton's method from the secant estimate, kept inside
-// the bracket (a Newton step that leaves it is replaced by a bisection step),
-// 6 iterations.
+// Hermite interpolant reaches `target`, starting from the secant estimate and
+// kept inside the bracket (a step that leaves it is replaced by a bisection
+// step).  Double: the chord iteration s <- s - f(s) / f'(s0) with the slope
+// at the secant point (one reciprocal; GB300's double divide is costly),
+// 16 iterations -- it converges linearly with the ratio |1 - f'/f'(s0)|,
+// small over one step, onto the root the oracle's bisection finds.  Single:
+// Newton's method, 6 iterations.
 template <typename T>
 __device__ __forceinline__ T crossing_fraction(const T *y0, const T *y1, T h, T target, int m = 1)
 {
     T lo = T(0), hi = T(1);
     T f_lo = y0[m] - target;
     if (sizeof(T) == 8) {
-        for (int it = 0; it < BisectIters<T>::value; ++it) {
-            T mid = T(0.5) * (lo + hi);
-            T f_mid = hermite(y0[m], y0[4 + m], y1[m], y1[4 + m], h, mid) - target;
-            if ((f_mid > T(0)) == (f_lo > T(0))) {
-                lo = mid;
-                f_lo = f_mid;
-            } else {
-                hi = mid;
-            }
+        const T f_h = y1[m] - target;
+        T s = f_lo / (f_lo - f_h);
+        if (!(s > T(0) && s < T(1)))
+            s = T(0.5);
+        const T p0 = y0[m], m0 = h * y0[4 + m], p1 = y1[m], m1 = h * y1[4 + m];
+        const T s2 = s * s;
+        const T df = (T(6) * s2 - T(6) * s) * p0 + (T(3) * s2 - T(4) * s + T(1)) * m0 + (T(6) * s - T(6) * s2) * p1 +
+                     (T(3) * s2 - T(2) * s) * m1;
+        const T idf = recip(df);
+        for (int it = 0; it < 16; ++it) {
+            const T f = hermite(p0, y0[4 + m], p1, y1[4 + m], h, s) - target;
+            if ((f > T(0)) == (f_lo > T(0)))
+                lo = s;
+            else
+                hi = s;
+            T sn = s - f * idf;
+            if (!(sn >= lo && sn <= hi))
+                sn = T(0.5) * (lo + hi);
+            s = sn;
         }
-        return T(0.5) * (lo + hi);
+        return s;
     }
     const T f_hi = y1[m] - target;
     T s = f_lo / (f_lo - f_hi);

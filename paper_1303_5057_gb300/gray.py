@@ -25,7 +25,7 @@ ACTIVE, CAPTURED, ESCAPED, STEP_CAP, NONFINITE, EMPTY, EQUATOR = 0, 1, 2, 3, 4, 
 FP64, FP32, FP32_KAHAN, FP32_KAHAN_SEL64 = 0, 1, 2, 3
 STEP_BENCH, STEP_EQ2 = 0, 1
 RENDER_PIXELS64, RENDER_PIXELS32, RENDER_RECORD, RENDER_INVARIANTS = 0, 1, 3, 4
-EVAL_CHRISTOFFEL, EVAL_RHS, EVAL_INITIAL, EVAL_XI, EVAL_SINCOS = 0, 1, 2, 3, 4
+EVAL_CHRISTOFFEL, EVAL_RHS, EVAL_INITIAL, EVAL_XI, EVAL_SINCOS, EVAL_RECIP = 0, 1, 2, 3, 4, 5
 LAUNCH_PERSISTENT, LAUNCH_ONE_PER_THREAD = 0, 1
 GRID_CARTESIAN, GRID_POLAR = 0, 1
 RECORD = 17
@@ -389,8 +389,8 @@ def gray_eval(what, precision, inp, stream=None):
     """inp: float64 CUDA tensor of n rows (4, 10, 6 or 10 doubles by ``what``).
     Returns a float64 CUDA tensor of n rows (64, 8, 8 or 1 doubles)."""
     import torch
-    width_in = {EVAL_CHRISTOFFEL: 4, EVAL_RHS: 10, EVAL_INITIAL: 6, EVAL_XI: 10, EVAL_SINCOS: 1}[what]
-    width_out = {EVAL_CHRISTOFFEL: 64, EVAL_RHS: 8, EVAL_INITIAL: 8, EVAL_XI: 1, EVAL_SINCOS: 2}[what]
+    width_in = {EVAL_CHRISTOFFEL: 4, EVAL_RHS: 10, EVAL_INITIAL: 6, EVAL_XI: 10, EVAL_SINCOS: 1, EVAL_RECIP: 1}[what]
+    width_out = {EVAL_CHRISTOFFEL: 64, EVAL_RHS: 8, EVAL_INITIAL: 8, EVAL_XI: 1, EVAL_SINCOS: 2, EVAL_RECIP: 1}[what]
     inp = inp.contiguous()
     n = inp.numel() // width_in
     out = torch.empty((n, width_out), dtype=torch.float64, device=inp.device)
