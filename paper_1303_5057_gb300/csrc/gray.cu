@@ -547,8 +547,16 @@ template <int MODE> __global__ void __maxnreg__(96) trace32_kernel(TraceArgs A)
     float r_promote = -INFINITY;
     int steps = 0, euler = 0, remaps = 0, n64 = 0, used = 0;
     unsigned long long tot_steps = 0, tot_euler = 0;
+    bool pending = false; // this lane handed its ray off; its index is not yet on the list
 
     for (;;) {
+        if (SEL64) {
+            int rank;
+            const unsigned long long hb = warp_count(&A.ws->handoff, pending, lane, &rank);
+            if (pending)
+                v.L[hb + rank] = (int)id;
+            pending = false;
+        }
         // ---- refill idle lanes from the work queue (warp-uniform loop) ----
         while (!exhausted) {
             const unsigned idle = __ballot_sync(FULL, !has);
@@ -649,13 +657,8 @@ template <int MODE> __global__ void __maxnreg__(96) trace32_kernel(TraceArgs A)
                     v.S0[id] = make_int4(status, steps, euler, remaps);
                     v.S1[id] = make_int4(n64, epoch, used, handoff ? FLAG_DOUBLE_MODE : 0);
                     has = false;
+                    pending = handoff;
                 }
-            }
-            if (SEL64) {
-                int rank;
-                const unsigned long long hb = warp_count(&A.ws->handoff, handoff, lane, &rank);
-                if (handoff)
-                    v.L[hb + rank] = (int)id;
             }
         }
     }

@@ -525,7 +525,7 @@ __device__ __forceinline__ T crossing_fraction(const T *y0, const T *y1, T h, T 
 
 // Grid projection (Sec. 3): the point where the step first crosses the
 // equatorial plane theta = pi/2 (start state and pre-remap end state).
-template <typename T> __device__ inline void equator_crossing(const T *y0, const T *y1, T h, T *fin)
+template <typename T> __device__ __noinline__ void equator_crossing(const T *y0, const T *y1, T h, T *fin)
 {
     const T half_pi = T(0.5) * pi_v<T>();
     const T s = crossing_fraction(y0, y1, h, half_pi, 2);
@@ -538,7 +538,7 @@ template <typename T> __device__ inline void equator_crossing(const T *y0, const
 // fraction, Hermite for the other coordinates, then the pole remap of Eq. 3
 // applied to the interpolated point.
 template <typename T>
-__device__ inline void stop_surface(const T *y0, const T *y1, T h, T r_stop, T *fin)
+__device__ __noinline__ void stop_surface(const T *y0, const T *y1, T h, T r_stop, T *fin)
 {
     const T s = crossing_fraction(y0, y1, h, r_stop);
     for (int m = 0; m < 4; ++m)
