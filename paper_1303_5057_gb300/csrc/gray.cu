@@ -1128,15 +1128,24 @@ __global__ void plan_scan_kernel(unsigned long long *aux)
     }
 }
 
+// Neighbouring pixels mostly share a bucket: the lanes of a warp with the
+// same bucket take their queue positions with one atomic (match + popc).
 __global__ void plan_scatter_kernel(const ImageDev *imgs, int n_images, int64_t total, int64_t first_ray, int stride,
                                     int budget, const int4 *S0, unsigned long long *aux, int *order)
 {
+    const unsigned FULL = 0xffffffffu;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= total)
-        return;
-    const int b = plan_bucket(imgs, n_images, i, first_ray, stride, budget, S0);
-    const unsigned long long pos = atomicAdd(&aux[AUX_OFF + b], 1ull);
-    order[pos] = (int)(first_ray + i);
+    const bool valid = i < total;
+    const int b = valid ? plan_bucket(imgs, n_images, i, first_ray, stride, budget, S0) : -1;
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(FULL, b);
+    const int leader = __ffs(peers) - 1;
+    unsigned long long base = 0;
+    if (valid && lane == leader)
+        base = atomicAdd(&aux[AUX_OFF + b], (unsigned long long)__popc(peers));
+    base = __shfl_sync(FULL, base, leader);
+    if (valid)
+        order[base + __popc(peers & ((1u << lane) - 1u))] = (int)(first_ray + i);
 }
 
 // --------------------------------------------------------------------------
