@@ -506,15 +506,11 @@ def main():
     from paper_1303_5057_gb300 import build, gray
     from paper_1303_5057_gb300 import inputs as I
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
+    from paper_1303_5057_gb300 import replicas
+    me = replicas.from_env()
+    world, rank = me.world, me.rank
+    dist = replicas.init(me, "nccl")
+    if dist is None:
         torch.cuda.set_device(0)
     if rank == 0:
         build.build()
@@ -590,12 +586,8 @@ def main():
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(d) for a, b, c, d in ev]
     trace_ms = [b.elapsed_time(c) for a, b, c, d in ev]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * steps_per_pass * args.steps / (total_ms / 1000.0)
+    total_ms = replicas.max_over_ranks(dist, sum(step_ms), device="cuda")
+    value = replicas.job_rate(steps_per_pass * args.steps, total_ms, world)
     main_ms = statistics.mean(p[0] for p in pass_ms)
     zone_ms = statistics.mean(p[1] for p in pass_ms) if pass_ms[0][1] >= 0 else None
     probe_ms = statistics.mean(p[2] for p in pass_ms) if pass_ms[0][2] >= 0 and not args.no_plan else None
