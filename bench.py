@@ -44,9 +44,9 @@ SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0
 # DRAM bytes (read + write) of one launch of the dominant kernel (the
 # single-precision pass of this workload) from an ncu capture, see
-# profiles/trace32_kernel_kerr1024_sel64_planned.md: 140,282,624 read +
-# 58,024,448 written.
-TRAFFIC_BYTES = 198307072
+# profiles/trace32_kernel_kerr1024_sel64_planned.md: 140,533,248 read +
+# 67,580,672 written.
+TRAFFIC_BYTES = 208113920
 # FP64 non-tensor: 2 FP64 lanes per SM on this part.
 FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1000.0
 
