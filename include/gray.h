@@ -113,7 +113,7 @@ typedef struct gray_options {
     int32_t precision;     /* GRAY_FP64 ... GRAY_FP32_KAHAN_SEL64 */
     int32_t step_rule;     /* GRAY_STEP_BENCH or GRAY_STEP_EQ2 */
     int32_t max_steps;     /* per-ray cap over all gray_trace calls, >= 1 */
-    int32_t block;         /* threads per block of the trace kernel (multiple of 32, 32..1024), 0 = default */
+    int32_t block;         /* threads per block of the single-precision trace kernel (multiple of 32, 32..1024), 0 = default */
     int32_t blocks_per_sm; /* resident blocks per SM of the persistent grid, 0 = default */
     int32_t refill;        /* steps between warp refills from the work queue, 0 = default */
     int32_t launch;        /* GRAY_LAUNCH_PERSISTENT or GRAY_LAUNCH_ONE_PER_THREAD (single precision only) */

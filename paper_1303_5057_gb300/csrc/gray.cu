@@ -1949,7 +1949,9 @@ int launch_pass(gray_ctx *ctx, const TraceArgs &A, int64_t work, cudaStream_t s)
     const int block = ctx->opt.block > 0 ? ctx->opt.block : 128;
     switch (ctx->opt.precision) {
     case GRAY_FP64:
-        trace64_kernel<<<persistent_grid(ctx, (const void *)trace64_kernel, block, work), block, 0, s>>>(A);
+        // the double kernels are built for 128-thread blocks (their launch
+        // bounds); the tunable block size is the single-precision pass's
+        trace64_kernel<<<persistent_grid(ctx, (const void *)trace64_kernel, 128, work), 128, 0, s>>>(A);
         break;
     case GRAY_FP32:
         trace32_kernel<GRAY_FP32>
@@ -2007,7 +2009,7 @@ int gray_trace(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, 
             //    climb out go to the return list (all counts stay on the
             //    device); 2. a single-precision pass over the return list;
             // 3. its hand-offs, in double with a single-precision tail.
-            const int block = ctx->opt.block > 0 ? ctx->opt.block : 128;
+            const int block = 128; // the zone kernels' launch bounds
             // rays spend only a few steps in the zone: refill lanes often
             TraceArgs Z = A;
             Z.refill = 1;

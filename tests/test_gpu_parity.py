@@ -406,6 +406,18 @@ def test_one_ray_per_thread_launch_equals_persistent(prec):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("prec", [gray.FP64, gray.FP32_KAHAN_SEL64])
+@pytest.mark.parametrize("shape", [dict(block=64), dict(block=256), dict(block=256, refill=32),
+                                   dict(blocks_per_sm=2, refill=4)])
+def test_launch_shape_does_not_change_results(prec, shape):
+    """Every launch shape the autotuner may pick is accepted by every pass
+    (the double passes keep their own block size) and gives the same bits."""
+    im = I.Image(a=0.9, incl=math.radians(75.0), nx=37, ny=29)
+    ref, _, _, _ = trace_image(im, gray.Options(precision=prec, max_steps=20000, r_sw=0.02))
+    got, _, _, _ = trace_image(im, gray.Options(precision=prec, max_steps=20000, r_sw=0.02, **shape))
+    assert np.array_equal(got, ref)
+
+
 def test_plan_puts_long_rays_first():
     """On a 256^2 image of the a = 0.99, i = 90 deg workload, the rays that
     take over 1000 steps sit in the first fifth of the planned queue."""
