@@ -77,7 +77,8 @@ def parse_args():
     p.add_argument("--rays", type=int, default=1 << 22, help="mixed workload: rays")
     p.add_argument("--images", type=int, default=256, help="sweep workload: images")
     p.add_argument("--rates", default="10,30,100,300,1000", help="serve workload: req/s")
-    p.add_argument("--requests", type=int, default=200, help="serve workload: requests per rate")
+    p.add_argument("--requests", type=int, default=0,
+                   help="serve workload: requests per rate (0: 60 s of arrivals, at least 200, at most 2000)")
     p.add_argument("--ring-nr", type=int, default=6000, help="rings workload: radii per angle")
     p.add_argument("--ring-nth", type=int, default=181, help="rings workload: angles")
     p.add_argument("--ring-out", default="", help="rings workload: write the per-image table here (JSON)")
@@ -313,11 +314,13 @@ def run_serve(args):
     out = []
     for rate in [float(x) for x in args.rates.split(",")]:
         srv = serve.Server(opt, capacity=16 << 20, round_budget=256)
-        reqs = I.request_stream(rate, args.requests)
-        st = srv.run(reqs, realtime=True, max_wall=60.0)
+        n_req = args.requests if args.requests > 0 else int(min(2000, max(200, 60.0 * rate)))
+        reqs = I.request_stream(rate, n_req)
+        st = srv.run(reqs, realtime=True, max_wall=180.0)
         srv.close()
         summ = st.summary()
         summ["rate_req_per_s"] = rate
+        summ["offered"] = n_req
         out.append(summ)
         print(json.dumps({"workload": "serve", "rate": rate, **summ}), flush=True)
     return 0
