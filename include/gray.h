@@ -208,8 +208,15 @@ int gray_setup_rays(gray_ctx *ctx, const double *rays_dev, int64_t n, double M,
  * host output was requested (the count is then unknown), or an error
  * (GRAY_EINVAL, GRAY_ECUDA).
  * In GRAY_FP32_KAHAN_SEL64 the call makes a single-precision pass over the
- * queue and then a pass over the rays that entered the zone near the horizon
- * (in double there, in compensated single precision once they leave it). */
+ * queue, then a double-precision pass over the rays that entered the zone
+ * near the horizon (rays climbing out of it are returned to a single-precision
+ * pass), then a last zone pass for the rays that came back to the zone (in
+ * double there, in compensated single precision once they leave it).  A ray's
+ * arithmetic does not depend on which pass runs it.  The zone r < cap_frac r_h
+ * + r_sw keeps the final angles of captured rays within 1e-4 rad of the FP64
+ * arithmetic at r_sw = 0.02 but for a few rays that cross the ergosurface,
+ * where the single-precision Eq. 4 test cannot resolve its threshold;
+ * r_sw = 0.9 (the ergoregion at the equator) removes those at ~3x the time. */
 int gray_trace(gray_ctx *ctx, void *state_dev, size_t state_bytes, int64_t n_state,
                const int32_t *order_dev, int64_t n_order, int64_t step_budget,
                int64_t *n_active_host, int64_t *stats_host, void *stream);
@@ -400,7 +407,7 @@ int gray_set_timing(gray_ctx *ctx, int32_t on);
 
 /* Durations of the last call's passes, in milliseconds (-1 where the pass did
  * not run or timing is off): ms_host[0] the single-precision (or FP64) pass
- * of gray_trace, ms_host[1] its zone pass (GRAY_FP32_KAHAN_SEL64), ms_host[2]
+ * of gray_trace, ms_host[1] its zone passes (GRAY_FP32_KAHAN_SEL64), ms_host[2]
  * the probe pass of gray_plan.  If zone_steps_host is not NULL it receives
  * the steps the zone pass took in the last gray_trace.  Waits for the events.
  * Errors: GRAY_EINVAL, GRAY_ECUDA. */
