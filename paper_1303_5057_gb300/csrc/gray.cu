@@ -188,6 +188,7 @@ namespace {
 
 struct ImageDev {
     double a, M, r_obs, incl;
+    double si, ci; // sin and cos of incl (host)
     double a0, da; // Cartesian: alpha of the first pixel edge, pixel width; polar: R0, dR
     double b0, db; // Cartesian: beta likewise; polar: first angle, angle step
     long long first; // first ray of the image relative to the call's first ray
@@ -263,7 +264,7 @@ __global__ void setup_images_kernel(const ImageDev *imgs, int n_images, int64_t 
     double alpha, beta;
     image_point(im, row, col, alpha, beta);
     double y[8];
-    initial_state(im.M, im.a, im.r_obs, im.incl, alpha, beta, y);
+    initial_state_sc(im.M, im.a, im.r_obs, im.si, im.ci, alpha, beta, y);
     store_initial(v, prec, first_ray + i, y, im.a, im.M, im.r_obs);
 }
 
@@ -1704,6 +1705,8 @@ ImageDev image_dev(const gray_image &im, int64_t first)
     d.M = im.M;
     d.r_obs = im.r_obs;
     d.incl = im.incl;
+    d.si = std::sin(im.incl);
+    d.ci = std::cos(im.incl);
     d.a0 = im.alpha0;
     d.da = (im.alpha1 - im.alpha0) / im.nx;
     d.b0 = im.beta0;

@@ -556,38 +556,45 @@ __device__ __noinline__ void stop_surface(const T *y0, const T *y1, T h, T r_sto
 // the pixel (alpha, beta) at distance D = r_obs, observer direction
 // n = (sin i, 0, cos i), photon moving along +n; k^t is the future root of the
 // null condition in the Kerr metric; k is scaled to unit energy E = -k_t.
-__device__ inline void initial_state(double M, double a, double r_obs, double incl, double alpha, double beta,
-                                     double *y)
+__device__ inline void initial_state_sc(double M, double a, double r_obs, double si, double ci, double alpha,
+                                        double beta, double *y)
 {
     const double D = r_obs;
-    double si, ci;
-    sincos(incl, &si, &ci);
     const double x = D * si - beta * ci;
     const double z = D * ci + beta * si;
     const double r = sqrt(D * D + alpha * alpha + beta * beta);
     const double rho = sqrt(x * x + alpha * alpha);
+    const double ir = recip(r), irho = recip(rho);
     const double th = atan2(rho, z);
     const double ph = atan2(alpha, x);
-    const double kr = D / r;
-    const double kth = (z * D - r * r * ci) / (rho * r * r);
-    const double kph = -alpha * si / (rho * rho);
+    const double kr = D * ir;
+    const double kth = (z * D - r * r * ci) * (irho * ir * ir);
+    const double kph = -alpha * si * (irho * irho);
     Hole<double> H = make_hole(a, M, r_obs, 1.0, 1.0, 0.0);
-    double s, c;
-    sincos(th, &s, &c);
+    // sin and cos of th = atan2(rho, z) with rho^2 + z^2 = r^2
+    const double s = rho * ir, c = z * ir;
     MetricPieces<double> m = metric_pieces(H, r, s, c);
     const double A = m.gtt;
     const double B = 2.0 * m.gtp * kph;
     const double C = m.grr * kr * kr + m.gthth * kth * kth + m.gpp * kph * kph;
-    const double kt = (-B - sqrt(B * B - 4.0 * A * C)) / (2.0 * A);
-    const double E = -(m.gtt * kt + m.gtp * kph);
+    const double kt = (-B - sqrt(B * B - 4.0 * A * C)) * (0.5 * recip(A));
+    const double iE = -recip(m.gtt * kt + m.gtp * kph);
     y[0] = 0.0;
     y[1] = r;
     y[2] = th;
     y[3] = ph;
-    y[4] = kt / E;
-    y[5] = kr / E;
-    y[6] = kth / E;
-    y[7] = kph / E;
+    y[4] = kt * iE;
+    y[5] = kr * iE;
+    y[6] = kth * iE;
+    y[7] = kph * iE;
+}
+
+__device__ inline void initial_state(double M, double a, double r_obs, double incl, double alpha, double beta,
+                                     double *y)
+{
+    double si, ci;
+    sincos(incl, &si, &ci);
+    initial_state_sc(M, a, r_obs, si, ci, alpha, beta, y);
 }
 
 } // namespace gray
