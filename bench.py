@@ -38,7 +38,11 @@ UNIT = "photon-steps/s"
 # states 37, RK4 combination 41, compensated update 32, Eq. 4 monitor 39,
 # step rule 6.
 F_STEP = 591
-SPECIAL_PER_STEP = {"sincos": 5, "div": 15}
+# Special-function work per step: one full sin/cos (the step's end point), three
+# by angle addition with short series (the interior stages, no SFU), and about
+# seven SFU reciprocals refined by Newton-Raphson (one per geometry, one or two
+# in the step size); ncu puts the SFU pipe at ~6 % busy, far from binding.
+SPECIAL_PER_STEP = {"sincos_full": 1, "sincos_by_angle_addition": 3, "sfu_reciprocal": 7}
 # FP32 non-tensor peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz.
 SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0
@@ -71,7 +75,8 @@ def parse_args():
     p.add_argument("--probe-budget", type=int, default=400)
     p.add_argument("--no-fp64-leg", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-rays", type=int, default=16384)
+    p.add_argument("--cpu-rays", type=int, default=262144,
+                   help="pixels of the CPU-baseline sample (~10 s on 16 cores); the reference arm takes 1/16 per step")
     p.add_argument("--workload", default="kerr1024",
                    choices=["kerr1024", "schwarzschild64", "mixed", "sweep", "serve", "projection", "rings", "view"])
     p.add_argument("--rays", type=int, default=1 << 22, help="mixed workload: rays")
@@ -169,7 +174,7 @@ def run_reference(args):
     from paper_1303_5057_gb300 import inputs as I
     im = I.kerr_1024(args.side).images[0]
     rule = 1 if args.step_rule == "eq2" else 0
-    per_step = max(256, args.cpu_rays // 4)
+    per_step = max(256, args.cpu_rays // 16)
     for _ in range(args.warmup):
         cpu_oracle_rate(im, 10000, rule, per_step)
     rates, steps_all, t_all = [], 0.0, 0.0
