@@ -524,7 +524,7 @@ __device__ __forceinline__ void warp_stats(const TraceArgs &A, int lane, unsigne
 }
 
 // Single-precision persistent tracer (modes FP32, FP32_KAHAN, FP32_KAHAN_SEL64).
-template <int MODE> __global__ void __maxnreg__(96) trace32_kernel(TraceArgs A)
+template <int MODE> __global__ void __maxnreg__(128) trace32_kernel(TraceArgs A)
 {
     constexpr bool KAHAN = ModeTraits<MODE>::kahan;
     constexpr bool SEL64 = ModeTraits<MODE>::sel64;
