@@ -2,6 +2,7 @@
 include/gray.h declares, and its host-side logic (layout sizes, defaults,
 argument validation that returns before any CUDA call) behaves."""
 import ctypes as C
+import os
 import re
 
 import pytest
@@ -71,6 +72,39 @@ def test_calls_reject_null_context(L):
     assert L.gray_plan(None, None, 0, 0, None, 0, 0, 4, 100, None, 0, None) == gray.EINVAL
     assert L.gray_render(None, None, 0, 0, 0, 0, 0, None, 0, None) == gray.EINVAL
     assert L.gray_shadow(None, None, 0, 0, 0, None, 0, None, 0, None) == gray.EINVAL
+    assert L.gray_ring(None, None, 0, 0, 0, None, 0, None, 0, None, 0, None) == gray.EINVAL
+    assert L.gray_splat(None, None, 0, 0, 0, 0, None, None, None, 0, None) == gray.EINVAL
+    assert L.gray_clear(None, None, 0, 0, 0, 0, None) == gray.EINVAL
+
+
+def test_structures_match_the_header(tmp_path):
+    """The binding's structures against the header as a C compiler lays it
+    out (sizes and the offsets of the fields added last)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stddef.h>
+#include <stdio.h>
+#include "gray.h"
+int main(void) {
+    printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gray_image), offsetof(gray_image, grid),
+           sizeof(gray_options), sizeof(gray_camera), offsetof(gray_camera, status_mask),
+           sizeof(gray_ring_info), sizeof(gray_shadow_info), sizeof(gray_pixel32));
+    return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.dirname(gray.HEADER), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = [ctypes.sizeof(gray._Image), gray._Image.grid.offset, ctypes.sizeof(gray._Options),
+            ctypes.sizeof(gray._Camera), gray._Camera.status_mask.offset, gray.RING_DTYPE.itemsize,
+            gray.SHADOW_DTYPE.itemsize, gray.PIXEL32_DTYPE.itemsize]
+    assert got == want
 
 
 def test_eval_rejects_bad_arguments(L):
