@@ -546,7 +546,8 @@ template <int MODE> __global__ void __maxnreg__(128) trace32_kernel(TraceArgs A)
     Hole<float> H;
     Geo<float> geo;
     float r_promote = -INFINITY;
-    int steps = 0, euler = 0, remaps = 0, n64 = 0, used = 0;
+    int steps = 0, euler = 0, remaps = 0, n64 = 0;
+    int steps0 = 0, euler0 = 0, used0 = 0; // at load: this call's counts follow from them
     unsigned long long tot_steps = 0, tot_euler = 0;
     bool pending = false; // this lane handed its ray off; its index is not yet on the list
 
@@ -591,7 +592,9 @@ template <int MODE> __global__ void __maxnreg__(128) trace32_kernel(TraceArgs A)
                             euler = s0.z;
                             remaps = s0.w;
                             n64 = s1.x;
-                            used = (s1.y == epoch) ? s1.z : 0;
+                            used0 = (s1.y == epoch) ? s1.z : 0;
+                            steps0 = steps;
+                            euler0 = euler;
                             H = make_hole_f(v.PF0[my], v.PF1[my], (float)A.cap_frac, (float)A.r_esc_frac,
                                             (float)A.r_sw);
                             r_promote = H.r_promote;
@@ -634,17 +637,13 @@ template <int MODE> __global__ void __maxnreg__(128) trace32_kernel(TraceArgs A)
                     status = GRAY_RAY_STEP_CAP;
                     for (int m = 0; m < 4; ++m)
                         fin[m] = y[m];
-                } else if (A.budget > 0 && used >= A.budget) {
+                } else if (A.budget > 0 && used0 + (steps - steps0) >= A.budget) {
                     yield = true;
                 } else if (SEL64 && y[1] - c[1] < r_promote) {
                     handoff = true;
                 } else {
-                    const int e0 = euler;
                     status = step_once<float, KAHAN>(H, O, y, c, geo, fin, euler, remaps);
-                    tot_euler += (unsigned long long)(euler - e0);
                     ++steps;
-                    ++used;
-                    ++tot_steps;
                 }
                 if (status != GRAY_RAY_ACTIVE || yield || handoff) {
                     st_f4(v.X, id, y[0], y[1], y[2], y[3]);
@@ -656,7 +655,9 @@ template <int MODE> __global__ void __maxnreg__(128) trace32_kernel(TraceArgs A)
                     if (status != GRAY_RAY_ACTIVE)
                         st_f4(v.F, id, fin[0], fin[1], fin[2], fin[3]);
                     v.S0[id] = make_int4(status, steps, euler, remaps);
-                    v.S1[id] = make_int4(n64, epoch, used, handoff ? FLAG_DOUBLE_MODE : 0);
+                    v.S1[id] = make_int4(n64, epoch, used0 + (steps - steps0), handoff ? FLAG_DOUBLE_MODE : 0);
+                    tot_steps += (unsigned long long)(steps - steps0);
+                    tot_euler += (unsigned long long)(euler - euler0);
                     has = false;
                     pending = handoff;
                 }
