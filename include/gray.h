@@ -73,7 +73,9 @@ extern "C" {
 #define GRAY_EVAL_INITIAL 2     /* in (M, a, r_obs, incl, alpha, beta) -> out y[8] */
 #define GRAY_EVAL_XI 3          /* in (M, a, y[8]) -> out xi of Eq. 4, 1 value */
 #define GRAY_EVAL_SINCOS 4      /* in (theta) -> out (sin, cos) as the tracer evaluates them, 2 values */
-#define GRAY_EVAL_RECIP 5       /* in (x) -> out 1/x as the tracer evaluates it, 1 value */
+#define GRAY_EVAL_RECIP 5       /* in (x) -> out 1/x as the tracer evaluates it: refined (step rule, */
+                                /* double everywhere) and, second, the single-precision geometry's  */
+                                /* hardware approximation; 2 values                                 */
 
 /* ---- launch of the trace kernel ------------------------------------- */
 #define GRAY_LAUNCH_PERSISTENT 0     /* persistent warps refilled from a work queue (default) */

@@ -1604,7 +1604,8 @@ template <typename T> __global__ void eval_kernel(int what, const double *in, in
         out[2 * i] = (double)sv;
         out[2 * i + 1] = (double)cv;
     } else if (what == GRAY_EVAL_RECIP) {
-        out[i] = (double)recip((T)in[i]);
+        out[2 * i] = (double)recip((T)in[i]);
+        out[2 * i + 1] = (double)recip_approx((T)in[i]);
     } else if (what == GRAY_EVAL_XI) {
         const double *q = in + 10 * i;
         const Hole<T> H = cast_hole<T>(make_hole(q[1], q[0], 1.0, 1.0, 1.0, 0.0));

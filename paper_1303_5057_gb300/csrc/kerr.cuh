@@ -51,7 +51,8 @@ template <> __device__ __forceinline__ double pi_v<double>() { return 3.14159265
 // Per-ray constants of the spacetime and of the stop surfaces.
 template <typename T> struct Hole {
     T a, M;
-    T a2, Ma, m2M; // a^2, M a, -2 M
+    T a2, Ma, m2M;     // a^2, M a, -2 M
+    T t2a, t2a2, t2Ma; // 2 a, 2 a^2, 2 M a
     T rp, rm, dc; // Delta = (r - rp)(r - rm) + dc
     T rp_lo;      // single precision: rp - (float)rp, so rp is carried to ~48 bits
     T r_h;        // horizon used by the step guard; -inf when M = 0 (no guard)
@@ -77,6 +78,9 @@ __host__ __device__ inline Hole<double> make_hole(double a, double M, double r_o
     H.a2 = a * a;
     H.Ma = M * a;
     H.m2M = -2.0 * M;
+    H.t2a = 2.0 * a;
+    H.t2a2 = 2.0 * H.a2;
+    H.t2Ma = 2.0 * H.Ma;
     double disc = M * M - a * a;
     double root = disc > 0.0 ? sqrt(disc) : 0.0;
     H.rp = M + root;
@@ -104,6 +108,9 @@ template <typename T> __host__ __device__ inline Hole<T> cast_hole(const Hole<do
     o.a2 = o.a * o.a;
     o.Ma = o.M * o.a;
     o.m2M = T(-2) * o.M;
+    o.t2a = T(2) * o.a;
+    o.t2a2 = T(2) * o.a2;
+    o.t2Ma = T(2) * o.Ma;
     o.rp = (T)h.rp;
     o.rp_lo = (T)(h.rp - (double)o.rp);
     o.rm = (T)h.rm;
@@ -139,6 +146,9 @@ __device__ __forceinline__ Hole<float> make_hole_f(float4 c0, float4 c1, float c
     H.a2 = H.a * H.a;
     H.Ma = H.M * H.a;
     H.m2M = -2.0f * H.M;
+    H.t2a = 2.0f * H.a;
+    H.t2a2 = 2.0f * H.a2;
+    H.t2Ma = 2.0f * H.Ma;
     H.rp = c0.z;
     H.rp_lo = c0.w;
     H.rm = c1.x;
@@ -255,6 +265,16 @@ __device__ __forceinline__ double recip(double x)
     return fma(r, e, r);
 }
 
+// The hardware reciprocal alone (within 1 ulp): single precision takes it
+// for the geometry of a point, whose other operations round as much.
+__device__ __forceinline__ float recip_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double recip_approx(double x) { return recip(x); }
+
 // Geometry of one point (r, theta): the quantities every right-hand side and
 // the Eq. 4 monitor need.  Single precision takes the three reciprocals from
 // one reciprocal of Sigma Delta sin(theta).
@@ -266,7 +286,7 @@ template <typename T> struct Geo {
 template <typename T> __device__ __forceinline__ void geometry_reciprocals(Geo<T> &g)
 {
     const T Ds = g.Delta * g.s, SD = g.Sigma * g.Delta;
-    const T inv = recip(SD * g.s);
+    const T inv = recip_approx(SD * g.s);
     g.iS = inv * Ds;
     g.iD = inv * (g.Sigma * g.s);
     g.is = inv * SD;
@@ -298,19 +318,17 @@ __device__ __forceinline__ Geo<T> geometry(const Hole<T> &H, T r, T th, T dr = T
     return g;
 }
 
-// sin and cos of a small angle d by their Taylor series: |d| <= 0.25,
-// truncation below 1e-11 (single, degrees 7 and 8) and 3e-18 (double,
-// degrees 11 and 12).  Returns false for larger |d|.
+// sin and cos of a small angle d by their Taylor series: single precision
+// for |d| <= 0.125 (degrees 5 and 6, truncation below 1e-10), double for
+// |d| <= 0.25 (degrees 11 and 12, below 3e-18).  Returns false for larger |d|.
 __device__ __forceinline__ bool small_sincos(float d, float *s, float *c)
 {
-    if (!(fabsf(d) <= 0.25f))
+    if (!(fabsf(d) <= 0.125f))
         return false;
     const float d2 = d * d;
-    float ps = fmaf(d2, -1.98412698e-04f, 8.33333333e-03f);
-    ps = fmaf(ps, d2, -1.66666667e-01f);
+    const float ps = fmaf(d2, 8.33333333e-03f, -1.66666667e-01f);
     *s = fmaf(ps * d2, d, d);
-    float pc = fmaf(d2, 2.48015873e-05f, -1.38888889e-03f);
-    pc = fmaf(pc, d2, 4.16666667e-02f);
+    float pc = fmaf(d2, -1.38888889e-03f, 4.16666667e-02f);
     pc = fmaf(pc, d2, -0.5f);
     *c = fmaf(pc, d2, 1.0f);
     return true;
@@ -359,66 +377,64 @@ __device__ __forceinline__ Geo<T> geometry_rel(const Hole<T> &H, const Geo<T> &g
 }
 
 // dk^mu/dl at a point whose geometry is known: the closed-form symbols
-// contracted with k k, grouped with w = k^t - a s^2 k^ph, iSw = w / Sigma,
-// A = r^2 - a^2 c^2 = 2 r^2 - Sigma, P = r^2 + a^2:
-//   a^t  = -2M/Sigma [ k^r/Delta (P A iSw - 2 a r^2 s^2 k^ph) - 2 a^2 r s c k^th iSw ]
-//   a^r  = [ -M A Delta iSw^2 + Delta r (s^2 k^ph^2 + k^th^2)
-//            - (a^2 r s^2 - M A) k^r^2/Delta + 2 a^2 s c k^r k^th ] / Sigma
-//   a^th = [ s c (2 M a^2 r iSw^2 - 4 M a r iSw k^ph + P k^ph^2
-//                 + a^2 (k^th^2 - k^r^2/Delta)) - 2 r k^r k^th ] / Sigma
-//   a^ph = -2 [ k^r/Delta (M a A iSw/Sigma + r k^ph (1 - 2 M r/Sigma))
-//               + cot(th) k^th (k^ph - 2 M a r iSw/Sigma) ]
+// contracted with k k, grouped with X = (k^t - a s^2 k^ph)/Sigma,
+// V = -2 a s^2 k^ph (so X = (k^t + V/2)/Sigma), u = k^r/Delta, q = k^r u,
+// Z = 2 M a r X, A = r^2 - a^2 c^2 = 2 r^2 - Sigma, P = r^2 + a^2:
+//   a^t  = -2M/Sigma [ u (P A X + r^2 V) - 2 a^2 r s c k^th X ]
+//   a^r  = [ M A (q - Delta X^2) + Delta r (s^2 k^ph^2 + k^th^2)
+//            - a^2 r s^2 q + 2 a^2 s c k^r k^th ] / Sigma
+//   a^th = [ s c (Z (a X - 2 k^ph) + P k^ph^2 + a^2 (k^th^2 - q))
+//            - 2 r k^r k^th ] / Sigma
+//   a^ph = -2 [ u ((M a A X - 2 M r^2 k^ph)/Sigma + r k^ph)
+//               + cot(th) k^th (k^ph - Z/Sigma) ]
 template <typename T>
 __device__ __forceinline__ void accel_geo(const Hole<T> &H, const Geo<T> &g, T kt, T kr, T kh, T kp, T *acc)
 {
-    const T a = H.a, M = H.M, a2 = H.a2;
-    const T r = g.r, iS = g.iS, iD = g.iD, Delta = g.Delta;
+    const T r = g.r, iS = g.iS;
     const T r2 = r * r, s2 = g.s * g.s, sc = g.s * g.c;
     const T A = fma(T(2), r2, -g.Sigma);
-    const T P = r2 + a2;
-    const T as2 = a * s2;
-    const T iSw = iS * fma(-as2, kp, kt);
-    const T Mr = M * r;
-    const T kr2 = kr * kr, krkh = kr * kh, khkh = kh * kh, kpkp = kp * kp;
-    const T iDkr = iD * kr;
-    const T a2r = a2 * r;
+    const T P = r2 + H.a2;
+    const T V = -(H.t2a * s2) * kp;
+    const T X = fma(V, T(0.5), kt) * iS;
+    const T u = kr * g.iD;
+    const T q = kr * u;
+    const T krkh = kr * kh, kh2 = kh * kh, kp2 = kp * kp;
     // t
-    const T u_t = fma(T(-2) * (r2 * as2), kp, (P * A) * iSw);
-    const T x_t = (a2r * sc) * (kh * iSw);
-    acc[0] = (H.m2M * iS) * fma(iDkr, u_t, T(-2) * x_t);
+    const T ut = fma(P * A, X, r2 * V);
+    const T xt = -(H.t2a2 * (r * sc)) * (kh * X);
+    acc[0] = (H.m2M * iS) * fma(u, ut, xt);
     // r
-    const T iSw2 = iSw * iSw;
-    const T MA = M * A;
-    const T t1 = (MA * Delta) * iSw2;
-    const T t2 = (Delta * r) * fma(s2, kpkp, khkh);
-    const T t3 = fma(a2r, s2, -MA) * (iD * kr2);
-    const T t4 = (a2 * sc) * krkh;
-    acc[1] = iS * fma(T(2), t4, (t2 - t1) - t3);
+    const T DX = g.Delta * X;
+    T sr = fma(H.M * A, fma(-DX, X, q), (g.Delta * r) * fma(s2, kp2, kh2));
+    sr = fma(-((H.a2 * r) * s2), q, sr);
+    sr = fma(H.t2a2 * sc, krkh, sr);
+    acc[1] = iS * sr;
     // theta
-    const T U2 = (Mr * a) * iSw;
-    const T h_in = fma(T(2) * (M * a2r), iSw2, fma(T(-4) * U2, kp, fma(P, kpkp, a2 * fma(-iD, kr2, khkh))));
-    acc[2] = iS * fma(sc, h_in, T(-2) * r * krkh);
+    const T Z = (H.t2Ma * r) * X;
+    const T hth = fma(Z, fma(H.a, X, T(-2) * kp), fma(P, kp2, H.a2 * (kh2 - q)));
+    acc[2] = iS * fma(r * krkh, T(-2), sc * hth);
     // phi
-    const T cot = g.c * g.is;
-    const T up1 = fma((H.Ma * A) * iS, iSw, (r * kp) * fma(T(-2) * Mr, iS, T(1)));
-    const T up2 = fma(T(-2) * U2, iS, kp);
-    acc[3] = T(-2) * fma(iDkr, up1, (cot * kh) * up2);
+    const T inner = fma(iS, fma(H.m2M * r2, kp, (H.Ma * A) * X), r * kp);
+    const T up2 = fma(-Z, iS, kp);
+    acc[3] = T(-2) * fma(u, inner, ((g.c * g.is) * kh) * up2);
 }
 
 // Eq. 4 test without its division: |xi + 1| > eps  <=>
-// |num + g_tt (k^t)^2| > eps |g_tt (k^t)^2| (NaN fails, as in the oracle).
+// |g(k, k)| > eps |g_tt (k^t)^2| (NaN fails, as in the oracle).  The norm
+// g(k, k) = num + g_tt (k^t)^2 is taken in the metric's Carter-frame form
+//   g(k, k) = [s^2 v^2 - Delta w^2] / Sigma + Sigma ((k^r)^2/Delta + (k^th)^2),
+//   w = k^t - a s^2 k^ph,  v = (r^2 + a^2) k^ph - a k^t,
+// which is the same quadratic form in fewer operations.
 template <typename T> __device__ __forceinline__ bool xi_fails(const Hole<T> &H, const Geo<T> &g, const T *y, T eps)
 {
-    const T r = g.r, s2 = g.s * g.s, a2 = H.a * H.a;
-    const T twoMr = T(2) * H.M * r;
-    const T gtt = -(T(1) - twoMr * g.iS);
-    const T gtp = -twoMr * H.a * s2 * g.iS;
-    const T grr = g.Sigma * g.iD;
-    const T gpp = (r * r + a2 + twoMr * a2 * s2 * g.iS) * s2;
+    const T r = g.r, s2 = g.s * g.s;
     const T kt = y[4], kr = y[5], kh = y[6], kp = y[7];
-    const T num = grr * kr * kr + gpp * kp * kp + g.Sigma * kh * kh + T(2) * gtp * kt * kp;
-    const T den = gtt * kt * kt;
-    return !(fabs(num + den) <= eps * fabs(den));
+    const T w = fma(-(H.a * s2), kp, kt);
+    const T v = fma(fma(r, r, H.a2), kp, -(H.a * kt));
+    const T E = fma(s2 * v, v, -((g.Delta * w) * w));
+    const T norm = fma(g.Sigma, fma(kr * g.iD, kr, kh * kh), E * g.iS);
+    const T den = fma(H.m2M * r, g.iS, T(1)) * (kt * kt);
+    return !(fabs(norm) <= eps * fabs(den));
 }
 
 // dk^mu/dl = -Gamma^mu_ab k^a k^b, from the closed-form symbols grouped with

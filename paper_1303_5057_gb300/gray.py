@@ -390,7 +390,7 @@ def gray_eval(what, precision, inp, stream=None):
     Returns a float64 CUDA tensor of n rows (64, 8, 8 or 1 doubles)."""
     import torch
     width_in = {EVAL_CHRISTOFFEL: 4, EVAL_RHS: 10, EVAL_INITIAL: 6, EVAL_XI: 10, EVAL_SINCOS: 1, EVAL_RECIP: 1}[what]
-    width_out = {EVAL_CHRISTOFFEL: 64, EVAL_RHS: 8, EVAL_INITIAL: 8, EVAL_XI: 1, EVAL_SINCOS: 2, EVAL_RECIP: 1}[what]
+    width_out = {EVAL_CHRISTOFFEL: 64, EVAL_RHS: 8, EVAL_INITIAL: 8, EVAL_XI: 1, EVAL_SINCOS: 2, EVAL_RECIP: 2}[what]
     inp = inp.contiguous()
     n = inp.numel() // width_in
     out = torch.empty((n, width_out), dtype=torch.float64, device=inp.device)

@@ -139,23 +139,27 @@ def test_single_precision_sincos_error_bound():
 
 @pytest.mark.parametrize("prec,ulps", [(gray.FP64, 2.0), (gray.FP32, 2.0)])
 def test_reciprocal_error_bound(prec, ulps):
-    """The tracer's reciprocal (hardware approximation + Newton-Raphson: one
-    step in single, two in double) against the exact quotient of the same
-    argument: within 2 ulp over the magnitudes the tracer meets (Sigma Delta
-    sin theta from ~1e-12 near a pole at the horizon to ~1e13 far out) and
-    both signs."""
+    """The tracer's reciprocals against the exact quotient of the same
+    argument, over the magnitudes the tracer meets (Sigma Delta sin theta
+    from ~1e-12 near a pole at the horizon to ~1e13 far out) and both signs:
+    the refined one (hardware approximation + Newton-Raphson: one step in
+    single, two in double) within `ulps`; the single-precision geometry's
+    plain hardware approximation within 2 ulp (in double the two are the
+    same function)."""
     rng = np.random.default_rng(6)
     x = np.concatenate([np.geomspace(1e-12, 1e13, 4000), -np.geomspace(1e-6, 1e6, 500),
                         rng.uniform(0.5, 2.0, 4000), [1.0, 3.0, 7.0, 1e-3]])
     if prec == gray.FP32:
         x = x.astype(np.float32).astype(np.float64)
-    got = gray.gray_eval(gray.EVAL_RECIP, prec, dev(x[:, None])).cpu().numpy()[:, 0]
+    got = gray.gray_eval(gray.EVAL_RECIP, prec, dev(x[:, None])).cpu().numpy()
     ref = 1.0 / x
     if prec == gray.FP32:
         ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
     else:
         ulp = np.spacing(np.abs(ref))
-    assert np.all(np.abs(got - ref) <= ulps * ulp)
+        assert np.array_equal(got[:, 0], got[:, 1])
+    assert np.all(np.abs(got[:, 0] - ref) <= ulps * ulp)
+    assert np.all(np.abs(got[:, 1] - ref) <= 2 * ulp)
 
 
 # ------------------------------------------------------------- whole rays ---
