@@ -343,8 +343,9 @@ __device__ __forceinline__ double ninth(double h) { return h * (1.0 / 9.0); }
 // One step.  Returns the ray's new status; writes fin[4] when it stops.  g
 // holds the geometry of the current point on entry and of the new point on
 // exit, so the first RK4 stage reuses what the previous step's Eq. 4 test
-// computed.
-template <typename T, bool KAHAN>
+// computed.  MIXED_STOP (double steps of the single-precision zone tracer):
+// the stop surfaces are interpolated by stop_surface_mixed.
+template <typename T, bool KAHAN, bool MIXED_STOP = false>
 __device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, T *y, T *c, Geo<T> &g, T *fin,
                                          int &euler, int &remaps)
 {
@@ -404,10 +405,16 @@ __device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, 
         equator_crossing(y, y1, h, fin);
         status = GRAY_RAY_EQUATOR;
     } else if (y1[1] <= H.r_cap) {
-        stop_surface(y, y1, h, H.r_cap, fin);
+        if constexpr (MIXED_STOP)
+            stop_surface_mixed(y, y1, h, H.r_cap, fin);
+        else
+            stop_surface(y, y1, h, H.r_cap, fin);
         status = GRAY_RAY_CAPTURED;
     } else if (y1[1] >= H.r_esc && h * y1[5] > T(0)) {
-        stop_surface(y, y1, h, H.r_esc, fin);
+        if constexpr (MIXED_STOP)
+            stop_surface_mixed(y, y1, h, H.r_esc, fin);
+        else
+            stop_surface(y, y1, h, H.r_esc, fin);
         status = GRAY_RAY_ESCAPED;
     }
     if (status != GRAY_RAY_NONFINITE && remap_eq3<T, KAHAN>(y1, c1)) {
@@ -917,7 +924,7 @@ __global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
                 } else {
                     const int e0 = euler;
                     if (RETURN || dbl) {
-                        status = step_once<double, false>(Hd, Od, yd, cz, gd, find, euler, remaps);
+                        status = step_once<double, false, true>(Hd, Od, yd, cz, gd, find, euler, remaps);
                         ++n64;
                         ++tot_fp64;
                     } else {
