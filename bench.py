@@ -71,7 +71,7 @@ def parse_args():
     p.add_argument("--blocks-per-sm", type=int, default=0)
     p.add_argument("--refill", type=int, default=0)
     p.add_argument("--no-plan", action="store_true")
-    p.add_argument("--probe-stride", type=int, default=4)
+    p.add_argument("--probe-stride", type=int, default=6)
     p.add_argument("--probe-budget", type=int, default=400)
     p.add_argument("--no-fp64-leg", action="store_true")
     p.add_argument("--no-cpu", action="store_true")

@@ -24,7 +24,7 @@ class ShadowSweep:
     ``inputs.Image``).  opt: ``gray.Options``.  plan: order the queue
     longest-first with ``gray_plan`` (probe_stride, probe_budget)."""
 
-    def __init__(self, images, opt: gray.Options, plan: bool = True, probe_stride: int = 4,
+    def __init__(self, images, opt: gray.Options, plan: bool = True, probe_stride: int = 6,
                  probe_budget: int = 400, device="cuda"):
         import torch
         self.images = list(images)

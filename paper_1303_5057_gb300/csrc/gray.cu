@@ -397,29 +397,35 @@ __device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, 
 #pragma unroll
     for (int m = 0; m < 8; ++m)
         finite &= isfinite(y1[m]);
-    if (!finite) {
-        status = GRAY_RAY_NONFINITE;
-        for (int m = 0; m < 4; ++m)
-            fin[m] = y1[m];
-    } else if (O.stop_equator && (y[2] - T(0.5) * pi_v<T>()) * (y1[2] - T(0.5) * pi_v<T>()) < T(0)) {
-        equator_crossing(y, y1, h, fin);
-        status = GRAY_RAY_EQUATOR;
-    } else if (y1[1] <= H.r_cap) {
-        if constexpr (MIXED_STOP)
-            stop_surface_mixed(y, y1, h, H.r_cap, fin);
-        else
-            stop_surface(y, y1, h, H.r_cap, fin);
-        status = GRAY_RAY_CAPTURED;
-    } else if (y1[1] >= H.r_esc && h * y1[5] > T(0)) {
-        if constexpr (MIXED_STOP)
-            stop_surface_mixed(y, y1, h, H.r_esc, fin);
-        else
-            stop_surface(y, y1, h, H.r_esc, fin);
-        status = GRAY_RAY_ESCAPED;
-    }
-    if (status != GRAY_RAY_NONFINITE && remap_eq3<T, KAHAN>(y1, c1)) {
-        ++remaps;
-        g1 = geometry(H, y1[1], y1[2], KAHAN ? -c1[1] : T(0), KAHAN ? -c1[2] : T(0));
+    // The rare outcomes (a non-finite state, a stop, a pole crossing) sit
+    // behind one test, so a plain step takes a single branch here.
+    const T half_pi = T(0.5) * pi_v<T>();
+    const bool equator = O.stop_equator && (y[2] - half_pi) * (y1[2] - half_pi) < T(0);
+    if (!finite || equator || y1[1] <= H.r_cap || y1[1] >= H.r_esc || y1[2] > pi_v<T>() || y1[2] < T(0)) {
+        if (!finite) {
+            status = GRAY_RAY_NONFINITE;
+            for (int m = 0; m < 4; ++m)
+                fin[m] = y1[m];
+        } else if (equator) {
+            equator_crossing(y, y1, h, fin);
+            status = GRAY_RAY_EQUATOR;
+        } else if (y1[1] <= H.r_cap) {
+            if constexpr (MIXED_STOP)
+                stop_surface_mixed(y, y1, h, H.r_cap, fin);
+            else
+                stop_surface(y, y1, h, H.r_cap, fin);
+            status = GRAY_RAY_CAPTURED;
+        } else if (y1[1] >= H.r_esc && h * y1[5] > T(0)) {
+            if constexpr (MIXED_STOP)
+                stop_surface_mixed(y, y1, h, H.r_esc, fin);
+            else
+                stop_surface(y, y1, h, H.r_esc, fin);
+            status = GRAY_RAY_ESCAPED;
+        }
+        if (status != GRAY_RAY_NONFINITE && remap_eq3<T, KAHAN>(y1, c1)) {
+            ++remaps;
+            g1 = geometry(H, y1[1], y1[2], KAHAN ? -c1[1] : T(0), KAHAN ? -c1[2] : T(0));
+        }
     }
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
@@ -555,6 +561,7 @@ template <int MODE> __global__ void __maxnreg__(128) trace32_kernel(TraceArgs A)
     float r_promote = -INFINITY;
     int steps = 0, euler = 0, remaps = 0, n64 = 0;
     int steps0 = 0, euler0 = 0, used0 = 0; // at load: this call's counts follow from them
+    int stop_at = 0;                        // step count at which the ray hits the cap or its budget
     unsigned long long tot_steps = 0, tot_euler = 0;
     bool pending = false; // this lane handed its ray off; its index is not yet on the list
 
@@ -602,6 +609,12 @@ template <int MODE> __global__ void __maxnreg__(128) trace32_kernel(TraceArgs A)
                             used0 = (s1.y == epoch) ? s1.z : 0;
                             steps0 = steps;
                             euler0 = euler;
+                            stop_at = A.max_steps;
+                            if (A.budget > 0) {
+                                const int64_t b = (int64_t)steps0 + A.budget - used0;
+                                if (b < stop_at)
+                                    stop_at = (int)b;
+                            }
                             H = make_hole_f(v.PF0[my], v.PF1[my], (float)A.cap_frac, (float)A.r_esc_frac,
                                             (float)A.r_sw);
                             r_promote = H.r_promote;
@@ -640,14 +653,16 @@ template <int MODE> __global__ void __maxnreg__(128) trace32_kernel(TraceArgs A)
             if (has) {
                 int status = GRAY_RAY_ACTIVE;
                 bool yield = false;
-                if (steps >= A.max_steps) {
-                    status = GRAY_RAY_STEP_CAP;
-                    for (int m = 0; m < 4; ++m)
-                        fin[m] = y[m];
-                } else if (A.budget > 0 && used0 + (steps - steps0) >= A.budget) {
-                    yield = true;
-                } else if (SEL64 && y[1] - c[1] < r_promote) {
-                    handoff = true;
+                if (steps >= stop_at || (SEL64 && y[1] - c[1] < r_promote)) {
+                    if (steps >= A.max_steps) {
+                        status = GRAY_RAY_STEP_CAP;
+                        for (int m = 0; m < 4; ++m)
+                            fin[m] = y[m];
+                    } else if (A.budget > 0 && used0 + (steps - steps0) >= A.budget) {
+                        yield = true;
+                    } else {
+                        handoff = true;
+                    }
                 } else {
                     status = step_once<float, KAHAN>(H, O, y, c, geo, fin, euler, remaps);
                     ++steps;

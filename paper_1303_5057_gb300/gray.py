@@ -278,7 +278,7 @@ def gray_trace(ctx, state, n_state, step_budget=0, wait=True, stream=None, order
     return rc, None, None
 
 
-def gray_plan(ctx, state, n_state, images, first_ray=0, probe_stride=4, probe_budget=400, order=None, stream=None):
+def gray_plan(ctx, state, n_state, images, first_ray=0, probe_stride=6, probe_budget=400, order=None, stream=None):
     """Longest-first work queue (int32 CUDA tensor) for the rays of ``images``
     set up at ``first_ray``; the probe rays advance by up to probe_budget."""
     import torch
@@ -437,7 +437,7 @@ class Tracer:
     def trace(self, step_budget=0, wait=True, stream=None, order=None):
         return gray_trace(self.ctx, self.state, self.n, step_budget, wait, stream, order)
 
-    def plan(self, images, first_ray=0, probe_stride=4, probe_budget=400, order=None, stream=None):
+    def plan(self, images, first_ray=0, probe_stride=6, probe_budget=400, order=None, stream=None):
         return gray_plan(self.ctx, self.state, self.n, images, first_ray, probe_stride, probe_budget, order, stream)
 
     def render(self, kind, first_ray=0, n=None, out=None, stream=None):
