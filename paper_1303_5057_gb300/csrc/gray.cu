@@ -194,6 +194,7 @@ struct ImageDev {
     long long first; // first ray of the image relative to the call's first ray
     int nx, ny;
     int grid, pad;
+    float hc[8]; // single-precision per-ray constants (hole_constants_f), once per image
 };
 
 // Image-plane position of the ray in (row, col) of an image: a pixel centre
@@ -216,8 +217,9 @@ __device__ __forceinline__ void image_point(const ImageDev &im, int64_t row, int
 // Store one initial state (double) into the layout of `prec`.  FP32 modes keep
 // the rounding error of each component in the compensation plane, so a
 // compensated trace starts from the double-precision initial condition.
+// hc: the single-precision constants of (a, M, r_obs), or NULL to compute them.
 __device__ void store_initial(const StateView &v, int prec, int64_t i, const double *y, double a, double M,
-                              double r_obs)
+                              double r_obs, const float *hc)
 {
     if (prec == GRAY_FP64) {
         st_d4(v.X, i, y[0], y[1], y[2], y[3]);
@@ -235,7 +237,12 @@ __device__ void store_initial(const StateView &v, int prec, int64_t i, const dou
         st_f4(v.CK, i, lo[4], lo[5], lo[6], lo[7]);
         st_f4(v.F, i, hi[0], hi[1], hi[2], hi[3]);
         float c8[8];
-        hole_constants_f(a, M, r_obs, c8);
+        if (hc) {
+            for (int m = 0; m < 8; ++m)
+                c8[m] = hc[m];
+        } else {
+            hole_constants_f(a, M, r_obs, c8);
+        }
         v.PF0[i] = make_float4(c8[0], c8[1], c8[2], c8[3]);
         v.PF1[i] = make_float4(c8[4], c8[5], c8[6], c8[7]);
     }
@@ -265,7 +272,7 @@ __global__ void setup_images_kernel(const ImageDev *imgs, int n_images, int64_t 
     image_point(im, row, col, alpha, beta);
     double y[8];
     initial_state_sc(im.M, im.a, im.r_obs, im.si, im.ci, alpha, beta, y);
-    store_initial(v, prec, first_ray + i, y, im.a, im.M, im.r_obs);
+    store_initial(v, prec, first_ray + i, y, im.a, im.M, im.r_obs, im.hc);
 }
 
 __global__ void setup_rays_kernel(const double *rays, int64_t n, double M, int64_t first_ray, StateView v, int prec)
@@ -276,7 +283,7 @@ __global__ void setup_rays_kernel(const double *rays, int64_t n, double M, int64
     const double *q = rays + 5 * i;
     double y[8];
     initial_state(M, q[2], q[4], q[3], q[0], q[1], y);
-    store_initial(v, prec, first_ray + i, y, q[2], M, q[4]);
+    store_initial(v, prec, first_ray + i, y, q[2], M, q[4], nullptr);
 }
 
 // --------------------------------------------------------------------------
@@ -1743,6 +1750,7 @@ ImageDev image_dev(const gray_image &im, int64_t first)
     d.ny = im.ny;
     d.grid = im.grid;
     d.pad = 0;
+    hole_constants_f(im.a, im.M, im.r_obs, d.hc);
     return d;
 }
 

@@ -620,15 +620,22 @@ __device__ inline void initial_state_sc(double M, double a, double r_obs, double
     const double kr = D * ir;
     const double kth = (z * D - r * r * ci) * (irho * ir * ir);
     const double kph = -alpha * si * (irho * irho);
-    Hole<double> H = make_hole(a, M, r_obs, 1.0, 1.0, 0.0);
-    // sin and cos of th = atan2(rho, z) with rho^2 + z^2 = r^2
-    const double s = rho * ir, c = z * ir;
-    MetricPieces<double> m = metric_pieces(H, r, s, c);
-    const double A = m.gtt;
-    const double B = 2.0 * m.gtp * kph;
-    const double C = m.grr * kr * kr + m.gthth * kth * kth + m.gpp * kph * kph;
+    // the metric at the start point; sin and cos of th = atan2(rho, z) with
+    // rho^2 + z^2 = r^2 (reciprocals, no divides: far from the horizon
+    // Delta = r (r - 2M) + a^2 does not cancel)
+    const double s = rho * ir, c = z * ir, s2 = s * s, a2 = a * a;
+    const double Sigma = fma(a2, c * c, r * r);
+    const double iS = recip(Sigma);
+    const double twoMr = 2.0 * M * r;
+    const double gtt = twoMr * iS - 1.0;
+    const double gtp = -(twoMr * a) * s2 * iS;
+    const double grr = Sigma * recip(fma(r, r - 2.0 * M, a2));
+    const double gpp = (r * r + a2 + (twoMr * a2) * s2 * iS) * s2;
+    const double A = gtt;
+    const double B = 2.0 * gtp * kph;
+    const double C = grr * kr * kr + Sigma * kth * kth + gpp * kph * kph;
     const double kt = (-B - sqrt(B * B - 4.0 * A * C)) * (0.5 * recip(A));
-    const double iE = -recip(m.gtt * kt + m.gtp * kph);
+    const double iE = -recip(gtt * kt + gtp * kph);
     y[0] = 0.0;
     y[1] = r;
     y[2] = th;
