@@ -48,9 +48,9 @@ SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0
 # DRAM bytes (read + write) of one launch of the dominant kernel (the
 # single-precision pass of this workload) from an ncu capture, see
-# profiles/trace32_kernel_kerr1024_sel64_planned.md: 140,345,600 read +
-# 65,613,312 written.
-TRAFFIC_BYTES = 205958912
+# profiles/trace32_kernel_kerr1024_sel64_planned.md: 140,259,072 read +
+# 66,909,440 written.
+TRAFFIC_BYTES = 207168512
 # FP64 non-tensor: 2 FP64 lanes per SM on this part.
 FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1000.0
 
