@@ -71,6 +71,8 @@ def parse_args():
     p.add_argument("--blocks-per-sm", type=int, default=0)
     p.add_argument("--refill", type=int, default=0)
     p.add_argument("--no-plan", action="store_true")
+    p.add_argument("--separate-setup", action="store_true",
+                   help="planned queue: gray_setup then gray_plan instead of the fused gray_setup_plan")
     p.add_argument("--probe-stride", type=int, default=6)
     p.add_argument("--probe-budget", type=int, default=400)
     p.add_argument("--no-fp64-leg", action="store_true")
@@ -540,27 +542,26 @@ def main():
 
     order_buf = torch.empty(n, dtype=torch.int32, device="cuda")
 
-    def plan_and_trace():
+    def setup_and_plan():
+        # planned: set-up and plan in one call (the non-probe set-up overlaps
+        # the probe pass); natural order: set-up alone
         if args.no_plan:
-            tr.trace(wait=False)
-        else:
-            order = tr.plan([im], probe_stride=args.probe_stride, probe_budget=args.probe_budget, order=order_buf)
-            tr.trace(wait=False, order=order)
+            tr.setup([im])
+            return None
+        if args.separate_setup:
+            tr.setup([im])
+            return tr.plan([im], probe_stride=args.probe_stride, probe_budget=args.probe_budget, order=order_buf)
+        return tr.setup_plan([im], probe_stride=args.probe_stride, probe_budget=args.probe_budget, order=order_buf)
 
     def one_step():
-        tr.setup([im])
-        plan_and_trace()
+        order = setup_and_plan()
+        tr.trace(wait=False, order=order)
         tr.render(gray.RENDER_PIXELS32, out=out_dev)
 
     # warm-up; the last warm-up step also reads the step statistics
     for _ in range(max(args.warmup, 1)):
         one_step()
-    tr.setup([im])
-    if not args.no_plan:
-        order = tr.plan([im], probe_stride=args.probe_stride, probe_budget=args.probe_budget, order=order_buf)
-        _, _, stats = tr.trace(order=order)
-    else:
-        _, _, stats = tr.trace()
+    _, _, stats = tr.trace(order=setup_and_plan())
     _, _, _, zone_steps = gray.gray_timings(tr.ctx)
     main_pass_steps = stats[0] - zone_steps  # steps of the dominant kernel (single-precision pass)
     rec = tr.records()
@@ -582,9 +583,9 @@ def main():
         flush.zero_()  # L2 flush between timed steps (outside the events)
         e0, e1, e2, e3 = ev[k]
         e0.record(stream)
-        tr.setup([im])
+        order = setup_and_plan()
         e1.record(stream)
-        plan_and_trace()
+        tr.trace(wait=False, order=order)
         e2.record(stream)
         tr.render(gray.RENDER_PIXELS32, out=out_dev)
         e3.record(stream)
@@ -593,6 +594,7 @@ def main():
     launches = gray.gray_launch_count() - launches0
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(d) for a, b, c, d in ev]
+    setup_plan_ms = [a.elapsed_time(b) for a, b, c, d in ev]  # set-up + plan (one call when planned)
     trace_ms = [b.elapsed_time(c) for a, b, c, d in ev]
     total_ms = replicas.max_over_ranks(dist, sum(step_ms), device="cuda")
     value = replicas.job_rate(steps_per_pass * args.steps, total_ms, world)
@@ -608,8 +610,7 @@ def main():
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        tr.setup([im])
-        plan_and_trace()
+        tr.trace(wait=False, order=setup_and_plan())
         tr.render(gray.RENDER_PIXELS32, out=out_dev)
         host_out.copy_(out_dev, non_blocking=True)
         torch.cuda.synchronize()
@@ -649,12 +650,14 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "kerr_a0.99_i90_%dx%d_%s" % (args.side, args.side, args.precision),
                        "rays": n, "max_steps": 10000, "step_rule": args.step_rule, "r_sw": args.r_sw,
-                       "queue": "natural" if args.no_plan else "planned (probe stride %d, budget %d)" % (
-                           args.probe_stride, args.probe_budget),
+                       "queue": "natural" if args.no_plan else "planned (probe stride %d, budget %d%s)" % (
+                           args.probe_stride, args.probe_budget,
+                           "; set-up, then plan" if args.separate_setup else
+                           "; set-up fused with the plan, non-probe set-up overlapping the probe pass"),
                        "l2": "flushed between timed steps (256 MB write)"},
             "ns_per_photon_step": 1e9 / (value / world),
             "steps_per_pass": steps_per_pass, "fp64_steps_per_pass": fp64_steps,
-            "trace_ms": statistics.mean(trace_ms),
+            "setup_plan_ms": statistics.mean(setup_plan_ms), "trace_ms": statistics.mean(trace_ms),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES,
                          "kernel": "trace32_kernel (single-precision pass)", "kernel_ms": main_ms,

@@ -240,6 +240,22 @@ int gray_plan(gray_ctx *ctx, void *state_dev, size_t state_bytes, int64_t n_stat
               int32_t probe_stride, int32_t probe_budget, int32_t *order_dev, size_t order_bytes,
               void *stream);
 
+/* gray_setup followed by gray_plan with the same images, first_ray, probe
+ * stride and budget, in one call: the probe rays are set up first on
+ * `stream`; the planning passes then run on a high-priority stream of the
+ * context (after everything queued so far on `stream`) while the other
+ * rays are set up on `stream` (the set-up is bound by the double-precision
+ * pipe, the probe pass by single-precision issue and latency, so the two
+ * share the SMs).  `stream` waits for the plan before the call's last
+ * operation, so work queued on it afterwards sees every ray set up and the
+ * queue written.  States and queue as from the two calls (the queue's order
+ * within a cost bucket is not deterministic).  The context's stream and
+ * events are created on the first call and freed by gray_destroy.
+ * Errors: GRAY_EINVAL (as gray_setup and gray_plan), GRAY_ECUDA. */
+int gray_setup_plan(gray_ctx *ctx, const gray_image *images, int32_t n_images, void *state_dev,
+                    size_t state_bytes, int64_t n_state, int64_t first_ray, int32_t probe_stride,
+                    int32_t probe_budget, int32_t *order_dev, size_t order_bytes, void *stream);
+
 /* Read rays first_ray .. first_ray + n - 1 of the buffer into out_dev
  * (out_bytes bytes):
  *   GRAY_RENDER_PIXELS64    n gray_pixel64

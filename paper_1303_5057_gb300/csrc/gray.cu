@@ -178,6 +178,8 @@ struct gray_ctx {
     bool timing = false;               // record events around the passes of each call
     cudaEvent_t ev[6] = {};            // [0,1] single pass, [2,3] zone pass, [4,5] plan probe pass
     bool ev_used[3] = {false, false, false};
+    cudaStream_t side = nullptr;       // gray_setup_plan: the planning passes (high priority)
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace {
@@ -251,8 +253,12 @@ __device__ void store_initial(const StateView &v, int prec, int64_t i, const dou
     v.S1[i] = make_int4(0, 0, 0, 0);
 }
 
+// Set-up of the rays of a call's images.  probe_stride > 0 selects part of
+// them: probe rays (every probe_stride-th pixel of each row and column,
+// which_probes = 1) or the others (which_probes = 0); probe_stride = 0 sets
+// up every ray.
 __global__ void setup_images_kernel(const ImageDev *imgs, int n_images, int64_t total, int64_t first_ray,
-                                    StateView v, int prec)
+                                    StateView v, int prec, int probe_stride = 0, int which_probes = 0)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total)
@@ -268,6 +274,8 @@ __global__ void setup_images_kernel(const ImageDev *imgs, int n_images, int64_t 
     const ImageDev im = imgs[lo];
     const int64_t p = i - im.first;
     const int64_t row = p / im.nx, col = p - row * im.nx;
+    if (probe_stride > 0 && ((row % probe_stride == 0 && col % probe_stride == 0) ? 1 : 0) != which_probes)
+        return;
     double alpha, beta;
     image_point(im, row, col, alpha, beta);
     double y[8];
@@ -1871,6 +1879,12 @@ void gray_destroy(gray_ctx *ctx)
     for (int k = 0; k < 6; ++k)
         if (ctx->ev[k])
             cudaEventDestroy(ctx->ev[k]);
+    if (ctx->fork)
+        cudaEventDestroy(ctx->fork);
+    if (ctx->join)
+        cudaEventDestroy(ctx->join);
+    if (ctx->side)
+        cudaStreamDestroy(ctx->side);
     cudaFree(ctx->ws);
     cudaFree(ctx->aux);
     cudaFreeHost(ctx->ws_host);
@@ -2117,9 +2131,15 @@ int gray_trace(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, 
     return w.active ? 1 : 0;
 }
 
-int gray_plan(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, const gray_image *images,
+} // extern "C"
+
+namespace {
+
+// Argument checks shared by gray_plan and gray_setup_plan; fills the image
+// table and its ray count.
+int plan_args(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, const gray_image *images,
               int32_t n_images, int64_t first_ray, int32_t probe_stride, int32_t probe_budget, int32_t *order,
-              size_t order_bytes, void *stream)
+              size_t order_bytes, std::vector<ImageDev> &t, int64_t &total)
 {
     int rc = check_state(ctx, state, state_bytes, n_state);
     if (rc)
@@ -2130,20 +2150,24 @@ int gray_plan(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, c
     for (int k = 0; k < n_images; ++k)
         if ((rc = validate_image(images[k])))
             return rc;
-    int64_t total = 0;
-    std::vector<ImageDev> t = image_table(images, n_images, total);
+    t = image_table(images, n_images, total);
     if (first_ray + total > n_state || order_bytes < sizeof(int32_t) * (size_t)total)
         return GRAY_EINVAL;
-    cudaStream_t s = (cudaStream_t)stream;
-    void *dimg = nullptr;
-    if ((rc = upload_table(t.data(), t.size() * sizeof(ImageDev), s, &dimg)))
-        return rc;
-    const ImageDev *im = (const ImageDev *)dimg;
+    return GRAY_OK;
+}
+
+// The planning passes on stream s (image table `im` already on the device):
+// 1. the probe list (written into the order buffer), 2. the probes traced
+// under the probe budget, 3. predicted cost -> bucket histogram ->
+// descending offsets -> queue.  Only the probe rays' states are read.
+int plan_passes(gray_ctx *ctx, void *state, int64_t n_state, const gray_image *images, int32_t n_images,
+                const ImageDev *im, int64_t total, int64_t first_ray, int32_t probe_stride, int32_t probe_budget,
+                int32_t *order, cudaStream_t s)
+{
+    int rc;
     if (cudaMemsetAsync(ctx->aux, 0, AUX_WORDS * sizeof(unsigned long long), s) != cudaSuccess ||
         cudaMemsetAsync(ctx->ws, 0, sizeof(Workspace), s) != cudaSuccess)
         return GRAY_ECUDA;
-    // 1. the probe list (written into the order buffer), 2. the probes traced
-    // under the probe budget
     probe_list_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, probe_stride, order,
                                                           ctx->aux);
     if ((rc = check_launch()))
@@ -2167,7 +2191,6 @@ int gray_plan(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, c
         return rc;
     if (ctx->timing)
         cudaEventRecord(ctx->ev[5], s);
-    // 3. predicted cost -> bucket histogram -> descending offsets -> queue
     const StateView v = make_view(state, n_state, ctx->opt.precision);
     plan_hist_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, probe_stride, probe_budget,
                                                          v.S0, ctx->aux);
@@ -2178,7 +2201,82 @@ int gray_plan(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, c
         return rc;
     plan_scatter_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, probe_stride,
                                                             probe_budget, v.S0, ctx->aux, order);
-    rc = check_launch();
+    return check_launch();
+}
+
+} // namespace
+
+extern "C" {
+
+int gray_plan(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, const gray_image *images,
+              int32_t n_images, int64_t first_ray, int32_t probe_stride, int32_t probe_budget, int32_t *order,
+              size_t order_bytes, void *stream)
+{
+    std::vector<ImageDev> t;
+    int64_t total = 0;
+    int rc = plan_args(ctx, state, state_bytes, n_state, images, n_images, first_ray, probe_stride, probe_budget,
+                       order, order_bytes, t, total);
+    if (rc)
+        return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *dimg = nullptr;
+    if ((rc = upload_table(t.data(), t.size() * sizeof(ImageDev), s, &dimg)))
+        return rc;
+    rc = plan_passes(ctx, state, n_state, images, n_images, (const ImageDev *)dimg, total, first_ray, probe_stride,
+                     probe_budget, order, s);
+    cudaError_t e = cudaFreeAsync(dimg, s);
+    if (rc)
+        return rc;
+    return cuda_err(e);
+}
+
+int gray_setup_plan(gray_ctx *ctx, const gray_image *images, int32_t n_images, void *state, size_t state_bytes,
+                    int64_t n_state, int64_t first_ray, int32_t probe_stride, int32_t probe_budget, int32_t *order,
+                    size_t order_bytes, void *stream)
+{
+    std::vector<ImageDev> t;
+    int64_t total = 0;
+    int rc = plan_args(ctx, state, state_bytes, n_state, images, n_images, first_ray, probe_stride, probe_budget,
+                       order, order_bytes, t, total);
+    if (rc)
+        return rc;
+    if (!ctx->side) {
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming) != cudaSuccess)
+            return GRAY_ECUDA;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    void *dimg = nullptr;
+    if ((rc = upload_table(t.data(), t.size() * sizeof(ImageDev), s, &dimg)))
+        return rc;
+    const ImageDev *im = (const ImageDev *)dimg;
+    StateView v = make_view(state, n_state, ctx->opt.precision);
+    // the probe rays first, on the caller's stream
+    setup_images_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, v, ctx->opt.precision,
+                                                           probe_stride, 1);
+    if ((rc = check_launch()))
+        return rc;
+    // the planning passes on the context's high-priority stream, after
+    // everything queued so far on the caller's stream; the other rays' set-up
+    // (bound by the double-precision pipe) fills the SMs the probe pass (few,
+    // latency-bound warps) leaves free
+    if (cudaEventRecord(ctx->fork, s) != cudaSuccess || cudaStreamWaitEvent(ctx->side, ctx->fork, 0) != cudaSuccess)
+        return GRAY_ECUDA;
+    rc = plan_passes(ctx, state, n_state, images, n_images, im, total, first_ray, probe_stride, probe_budget, order,
+                     ctx->side);
+    if (cudaEventRecord(ctx->join, ctx->side) != cudaSuccess)
+        return GRAY_ECUDA;
+    if (!rc) {
+        setup_images_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, v,
+                                                               ctx->opt.precision, probe_stride, 0);
+        rc = check_launch();
+    }
+    // the caller's stream resumes only after the plan as well
+    if (cudaStreamWaitEvent(s, ctx->join, 0) != cudaSuccess)
+        return GRAY_ECUDA;
     cudaError_t e = cudaFreeAsync(dimg, s);
     if (rc)
         return rc;

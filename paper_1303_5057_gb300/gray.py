@@ -144,6 +144,8 @@ def lib():
     L.gray_trace.restype = C.c_int
     L.gray_plan.argtypes = [vp, vp, sz, i64, C.POINTER(_Image), i32, i64, i32, i32, vp, sz, vp]
     L.gray_plan.restype = C.c_int
+    L.gray_setup_plan.argtypes = [vp, C.POINTER(_Image), i32, vp, sz, i64, i64, i32, i32, vp, sz, vp]
+    L.gray_setup_plan.restype = C.c_int
     L.gray_trace.restype = C.c_int
     L.gray_clear.argtypes = [vp, vp, sz, i64, i64, i64, vp]
     L.gray_clear.restype = C.c_int
@@ -289,6 +291,21 @@ def gray_plan(ctx, state, n_state, images, first_ray=0, probe_stride=6, probe_bu
     _check(lib().gray_plan(ctx, _ptr(state), state.numel() * state.element_size(), int(n_state), arr, len(images),
                            int(first_ray), int(probe_stride), int(probe_budget), _ptr(order),
                            order.numel() * order.element_size(), _stream(stream)), "gray_plan")
+    return order[:total]
+
+
+def gray_setup_plan(ctx, images, state, n_state, first_ray=0, probe_stride=6, probe_budget=400, order=None,
+                    stream=None):
+    """gray_setup then gray_plan in one call, the set-up of the non-probe rays
+    overlapping the probe pass; returns the queue as gray_plan does."""
+    import torch
+    arr = _images(images)
+    total = sum(int(im.nx) * int(im.ny) for im in images)
+    if order is None:
+        order = torch.empty(max(1, total), dtype=torch.int32, device=state.device)
+    _check(lib().gray_setup_plan(ctx, arr, len(images), _ptr(state), state.numel() * state.element_size(),
+                                 int(n_state), int(first_ray), int(probe_stride), int(probe_budget), _ptr(order),
+                                 order.numel() * order.element_size(), _stream(stream)), "gray_setup_plan")
     return order[:total]
 
 
@@ -439,6 +456,10 @@ class Tracer:
 
     def plan(self, images, first_ray=0, probe_stride=6, probe_budget=400, order=None, stream=None):
         return gray_plan(self.ctx, self.state, self.n, images, first_ray, probe_stride, probe_budget, order, stream)
+
+    def setup_plan(self, images, first_ray=0, probe_stride=6, probe_budget=400, order=None, stream=None):
+        return gray_setup_plan(self.ctx, images, self.state, self.n, first_ray, probe_stride, probe_budget, order,
+                               stream)
 
     def render(self, kind, first_ray=0, n=None, out=None, stream=None):
         return gray_render(self.ctx, self.state, self.n, kind, first_ray, n, out, stream)

@@ -70,6 +70,7 @@ def test_calls_reject_null_context(L):
     assert L.gray_setup(None, None, 1, None, 0, 1, 0, None) == gray.EINVAL
     assert L.gray_trace(None, None, 0, 0, None, 0, 0, None, None, None) == gray.EINVAL
     assert L.gray_plan(None, None, 0, 0, None, 0, 0, 4, 100, None, 0, None) == gray.EINVAL
+    assert L.gray_setup_plan(None, None, 1, None, 0, 1, 0, 4, 100, None, 0, None) == gray.EINVAL
     assert L.gray_render(None, None, 0, 0, 0, 0, 0, None, 0, None) == gray.EINVAL
     assert L.gray_shadow(None, None, 0, 0, 0, None, 0, None, 0, None) == gray.EINVAL
     assert L.gray_ring(None, None, 0, 0, 0, None, 0, None, 0, None, 0, None) == gray.EINVAL

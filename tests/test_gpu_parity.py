@@ -444,6 +444,32 @@ def test_launch_shape_does_not_change_results(prec, shape):
     assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("prec", [gray.FP32_KAHAN_SEL64, gray.FP64])
+def test_setup_plan_equals_setup_then_plan(prec):
+    """The fused call (non-probe set-up on a side stream, overlapping the
+    probe pass) leaves every state as gray_setup + gray_plan do, queues the
+    same rays, and the traces that follow agree bit for bit."""
+    ims = [I.Image(a=0.9, incl=1.1, nx=41, ny=23), I.Image(a=-0.5, incl=0.4, nx=17, ny=30)]
+    n = sum(im.n for im in ims)
+    opt = gray.Options(precision=prec, max_steps=10000, r_sw=0.02)
+    out = []
+    for fused in (False, True):
+        tr = gray.Tracer(opt, n + 3)
+        if fused:
+            order = tr.setup_plan(ims, first_ray=3, probe_stride=5, probe_budget=120)
+        else:
+            tr.setup(ims, first_ray=3)
+            order = tr.plan(ims, first_ray=3, probe_stride=5, probe_budget=120)
+        after_plan = tr.records(first_ray=3, n=n)
+        o = np.sort(order.cpu().numpy())
+        tr.trace(order=order)
+        out.append((after_plan, o, tr.records(first_ray=3, n=n)))
+        tr.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[1][1], np.arange(3, 3 + n))
+    assert np.array_equal(out[0][2], out[1][2])
+
+
 def test_plan_puts_long_rays_first():
     """On a 256^2 image of the a = 0.99, i = 90 deg workload, the rays that
     take over 1000 steps sit in the first fifth of the planned queue."""
