@@ -2,7 +2,8 @@
 
 All images share one state buffer (image after image); one ``gray_setup``
 writes every initial state, one ``gray_plan`` orders every ray of every image
-longest-first, one ``gray_trace`` traces them all, and one ``gray_shadow``
+longest-first (the two fused in ``gray_setup_plan`` when planning), one
+``gray_trace`` traces them all, and one ``gray_shadow``
 reduces each image to its captured area, equivalent radius and centroid (the
 quantities behind the paper's photon-ring study, Sec. 4).  The trace step can
 be captured once in a CUDA graph and replayed for further batches of the same
@@ -44,10 +45,10 @@ class ShadowSweep:
 
     # -- the three phases -------------------------------------------------
     def setup(self, stream=None):
-        self.tracer.setup(self.images, stream=stream)
         if self.plan:
-            return self.tracer.plan(self.images, probe_stride=self.probe_stride, probe_budget=self.probe_budget,
-                                    order=self.order, stream=stream)
+            return self.tracer.setup_plan(self.images, probe_stride=self.probe_stride,
+                                          probe_budget=self.probe_budget, order=self.order, stream=stream)
+        self.tracer.setup(self.images, stream=stream)
         return None
 
     def trace(self, order=None, stream=None):
