@@ -395,8 +395,8 @@ int gray_splat(gray_ctx *ctx, const void *state_dev, size_t state_bytes, int64_t
  *
  * It writes the same initial states as gray_setup (bit for bit) for a
  * buffer laid out for `precision`.  The image table is copied into a
- * file-scope device array of GRAY_NOALLOC_MAX_IMAGES entries (104 bytes each,
- * 416 KB) that every device loading the library holds until the process
+ * file-scope device array of GRAY_NOALLOC_MAX_IMAGES entries (136 bytes each,
+ * 544 KB) that every device loading the library holds until the process
  * exits; n_images above that maximum is rejected with GRAY_EINVAL before any
  * work is enqueued.  On the first call on a device the library looks up that
  * array's device address (cudaGetSymbolAddress) with the device current and

@@ -198,6 +198,7 @@ struct ImageDev {
     int grid, pad;
     float hc[8]; // single-precision per-ray constants (hole_constants_f), once per image
 };
+static_assert(sizeof(ImageDev) == 136, "gray_setup_noalloc's table size is documented in gray.h");
 
 // Image-plane position of the ray in (row, col) of an image: a pixel centre
 // of the Cartesian grid, or the polar grid point of Sec. 4 (Eqs. 9-10).
