@@ -2241,14 +2241,13 @@ int gray_setup_plan(gray_ctx *ctx, const gray_image *images, int32_t n_images, v
                        order, order_bytes, t, total);
     if (rc)
         return rc;
-    if (!ctx->side) {
-        int least = 0, greatest = 0;
-        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
-            cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, greatest) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming) != cudaSuccess)
-            return GRAY_ECUDA;
-    }
+    int least = 0, greatest = 0;
+    if (!ctx->side && (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+                       cudaStreamCreateWithPriority(&ctx->side, cudaStreamNonBlocking, greatest) != cudaSuccess))
+        return GRAY_ECUDA;
+    if ((!ctx->fork && cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) != cudaSuccess) ||
+        (!ctx->join && cudaEventCreateWithFlags(&ctx->join, cudaEventDisableTiming) != cudaSuccess))
+        return GRAY_ECUDA;
     cudaStream_t s = (cudaStream_t)stream;
     void *dimg = nullptr;
     if ((rc = upload_table(t.data(), t.size() * sizeof(ImageDev), s, &dimg)))
@@ -2258,26 +2257,33 @@ int gray_setup_plan(gray_ctx *ctx, const gray_image *images, int32_t n_images, v
     // the probe rays first, on the caller's stream
     setup_images_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, v, ctx->opt.precision,
                                                            probe_stride, 1);
-    if ((rc = check_launch()))
-        return rc;
+    rc = check_launch();
     // the planning passes on the context's high-priority stream, after
     // everything queued so far on the caller's stream; the other rays' set-up
     // (bound by the double-precision pipe) fills the SMs the probe pass (few,
     // latency-bound warps) leaves free
-    if (cudaEventRecord(ctx->fork, s) != cudaSuccess || cudaStreamWaitEvent(ctx->side, ctx->fork, 0) != cudaSuccess)
-        return GRAY_ECUDA;
-    rc = plan_passes(ctx, state, n_state, images, n_images, im, total, first_ray, probe_stride, probe_budget, order,
-                     ctx->side);
-    if (cudaEventRecord(ctx->join, ctx->side) != cudaSuccess)
-        return GRAY_ECUDA;
     if (!rc) {
-        setup_images_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, v,
-                                                               ctx->opt.precision, probe_stride, 0);
-        rc = check_launch();
+        if (cudaEventRecord(ctx->fork, s) != cudaSuccess || cudaStreamWaitEvent(ctx->side, ctx->fork, 0) != cudaSuccess) {
+            rc = GRAY_ECUDA;
+        } else {
+            rc = plan_passes(ctx, state, n_state, images, n_images, im, total, first_ray, probe_stride, probe_budget,
+                             order, ctx->side);
+            const bool joined = cudaEventRecord(ctx->join, ctx->side) == cudaSuccess;
+            if (!rc) {
+                setup_images_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, v,
+                                                                       ctx->opt.precision, probe_stride, 0);
+                rc = check_launch();
+            }
+            // the caller's stream resumes only after the plan as well; if it
+            // cannot wait for it, nothing on the side stream may outlive the
+            // image table freed below
+            if (!joined || cudaStreamWaitEvent(s, ctx->join, 0) != cudaSuccess) {
+                cudaStreamSynchronize(ctx->side);
+                if (!rc)
+                    rc = GRAY_ECUDA;
+            }
+        }
     }
-    // the caller's stream resumes only after the plan as well
-    if (cudaStreamWaitEvent(s, ctx->join, 0) != cudaSuccess)
-        return GRAY_ECUDA;
     cudaError_t e = cudaFreeAsync(dimg, s);
     if (rc)
         return rc;
