@@ -161,8 +161,8 @@ struct Workspace {
     unsigned long long euler;   // Euler redos in this call
     unsigned long long fp64;    // steps taken in double by the selective mode in this call
     unsigned long long active;  // rays left active by this call
-    unsigned long long handoff; // rays appended to the hand-off list in this round
-    unsigned long long demoted; // rays returned to single precision in this round
+    unsigned long long handoff; // rays appended to the hand-off list by the current pass
+    unsigned long long demoted; // rays returned to single precision by the current zone pass
     unsigned long long zone_steps; // steps taken by the zone kernel in this call
 };
 
