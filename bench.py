@@ -192,8 +192,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_all / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "kerr_a0.99_i90_%dx%d" % (args.side, args.side), "rays": args.side ** 2,
-                       "max_steps": 10000, "step_rule": args.step_rule},
+            "config": {"workload": "kerr_a0.99_i90_%dx%d" % (args.side, args.side), "precision": "fp64 (oracle)",
+                       "rays": args.side ** 2, "max_steps": 10000, "step_rule": args.step_rule},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -648,7 +648,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "kerr_a0.99_i90_%dx%d_%s" % (args.side, args.side, args.precision),
+            "config": {"workload": "kerr_a0.99_i90_%dx%d" % (args.side, args.side), "precision": args.precision,
                        "rays": n, "max_steps": 10000, "step_rule": args.step_rule, "r_sw": args.r_sw,
                        "queue": "natural" if args.no_plan else "planned (probe stride %d, budget %d%s)" % (
                            args.probe_stride, args.probe_budget,
