@@ -40,9 +40,12 @@ UNIT = "photon-steps/s"
 F_STEP = 591
 # Special-function work per step: one full sin/cos (the step's end point), three
 # by angle addition with short series (the interior stages, no SFU), and about
-# seven SFU reciprocals refined by Newton-Raphson (one per geometry, one or two
-# in the step size); ncu puts the SFU pipe at ~6 % busy, far from binding.
+# seven SFU reciprocals (one per geometry, plain; one or two in the step size,
+# refined by a Newton-Raphson step); ncu puts the SFU pipe at ~6 % busy.  At
+# 16 SFU results per clock per SM the reciprocals alone would allow
+# 152 x 16 x 2.070e9 / 7 = 7.2e11 steps/s, far above the FMA bound.
 SPECIAL_PER_STEP = {"sincos_full": 1, "sincos_by_angle_addition": 3, "sfu_reciprocal": 7}
+SFU_PER_CLK_PER_SM = 16
 # FP32 non-tensor peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz.
 SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0
@@ -663,6 +666,8 @@ def main():
                          "kernel": "trace32_kernel (single-precision pass)", "kernel_ms": main_ms,
                          "kernel_steps": main_pass_steps,
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (FP32 non-tensor, max clock)",
+                         "sfu_bound_steps_per_s": SMS * SFU_PER_CLK_PER_SM * SM_MAX_GHZ * 1e9
+                         / SPECIAL_PER_STEP["sfu_reciprocal"],
                          "flop_per_step": F_STEP, "special_per_step": SPECIAL_PER_STEP},
             "passes_ms": {"single": main_ms, "zone": zone_ms, "probe": probe_ms,
                           "zone_steps": zone_steps, "setup_plan_trace_render": total_ms / args.steps},
