@@ -113,3 +113,13 @@ def test_eval_rejects_bad_arguments(L):
     assert L.gray_eval(gray.EVAL_RHS, gray.FP32_KAHAN, None, 1, None, None) == gray.EINVAL
     assert L.gray_eval(gray.EVAL_RHS, gray.FP64, None, -1, None, None) == gray.EINVAL
     assert L.gray_eval(gray.EVAL_RHS, gray.FP64, None, 0, None, None) == gray.OK
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libgray.so the binding raises: there is no fallback path."""
+    monkeypatch.setattr(gray, "_lib", None)
+    monkeypatch.setattr(gray, "LIB_PATH", str(tmp_path / "libgray.so"))
+    with pytest.raises(RuntimeError, match="libgray.so not found"):
+        gray.lib()
+    with pytest.raises(RuntimeError):
+        gray.Tracer(gray.Options(), 16)
