@@ -265,8 +265,9 @@ __device__ __forceinline__ double recip(double x)
     return fma(r, e, r);
 }
 
-// The hardware reciprocal alone (within 1 ulp): single precision takes it
-// for the geometry of a point, whose other operations round as much.
+// The hardware reciprocal alone (bounded by 2 ulp in a unit test): single
+// precision takes it for the geometry of a point, whose other operations
+// round as much; double keeps the refined one.
 __device__ __forceinline__ float recip_approx(float x)
 {
     float r;
@@ -276,8 +277,8 @@ __device__ __forceinline__ float recip_approx(float x)
 __device__ __forceinline__ double recip_approx(double x) { return recip(x); }
 
 // Geometry of one point (r, theta): the quantities every right-hand side and
-// the Eq. 4 monitor need.  Single precision takes the three reciprocals from
-// one reciprocal of Sigma Delta sin(theta).
+// the Eq. 4 monitor need.  The three reciprocals come from one reciprocal of
+// Sigma Delta sin(theta).
 template <typename T> struct Geo {
     T r, s, c, Sigma, Delta, iS, iD, is;
 };
