@@ -231,6 +231,51 @@ def test_kerr_fp32_selective_double_matches_oracle(r_sw):
     assert np.percentile(np.abs(gq[ok] - qd[ok]), 99) < 1e-5
 
 
+def _full_size_sample(prec, n_sample=4096):
+    """The bench workload at its full size (a = 0.99, i = 90 deg, 1024^2, cap
+    1e4) in the bench's launch configuration (set-up fused with the stride-6,
+    budget-400 plan; persistent trace; r_sw = 0.02), and the oracle on
+    n_sample evenly spread pixels of it, traced one by one."""
+    im = I.kerr_1024(1024).images[0]
+    tr = gray.Tracer(gray.Options(precision=prec, max_steps=10000, r_sw=0.02), im.n)
+    order = tr.setup_plan([im], probe_stride=6, probe_budget=400)
+    rc, n_active, _ = tr.trace(order=order)
+    rec = tr.records()
+    tr.close()
+    assert rc == 0 and n_active == 0
+    idx = np.unique(np.linspace(0, im.n - 1, n_sample).astype(np.int64))
+    rays = oracle.image_rays(im.a, im.incl, im.r_obs, im.nx, im.ny, im.alpha0, im.alpha1, im.beta0, im.beta1)[idx]
+    ref = oracle.trace_many(rays, oracle.Options(max_steps=10000))
+    far = P.band_mask((rays[:, 0], rays[:, 1]), im.a, im.incl)
+    sane = far & (P.oracle_q_drift(oracle, rays, ref) < P.SANE_Q)
+    return rec[idx], ref, far, sane
+
+
+def test_full_size_fp64_on_sampled_pixels():
+    """FP64 at the bench's full size and launch configuration: on 4096
+    sampled pixels, classification equal outside the band, final angles
+    within 1e-9 relative and identical step counts on the faithfully
+    integrated rays."""
+    rec, ref, far, sane = _full_size_sample(gray.FP64)
+    assert P.compare(rec, ref, far)["class_agree_far"] == 1.0
+    c = P.compare(rec, ref, sane)
+    assert c["n_compared"] > 2000, c
+    assert c["max_rel"] <= 1e-9 and c["steps_equal_frac"] == 1.0, c
+
+
+def test_full_size_bench_configuration_on_sampled_pixels():
+    """The bench line's own configuration (compensated FP32 + zone) at full
+    size: on 4096 sampled pixels, classification agrees on >= 99.9 % outside
+    the band, and at most 0.2 % of the faithfully integrated rays leave the
+    oracle's final angles by more than 1e-4 rad (the ergosurface rays of the
+    192 x 192 test: single-precision Eq. 4 decisions there)."""
+    rec, ref, far, sane = _full_size_sample(gray.FP32_KAHAN_SEL64)
+    assert P.compare(rec, ref, far)["class_agree_far"] >= 0.999
+    c = P.compare(rec, ref, sane)
+    assert c["n_compared"] > 2000, c
+    assert c["n_ang_gt_1e-4"] <= 0.002 * c["n_compared"], c
+
+
 def test_kerr_fp32_finer_grid_and_the_ergoregion():
     """The same image at 192 x 192.  With the default zone (r_sw = 0.02) a
     few rays outside the band (<= 0.05 %) leave the oracle's final angles by
