@@ -527,3 +527,69 @@ int orc_trace_many(int64_t n, const double *rays, const orc_options *o, double *
             pthread_join(th[t], NULL);
     return 0;
 }
+
+/* Start states of n image-plane rays (alpha, beta, a, incl, r_obs) -> n x 8. */
+void orc_initial_many(int64_t n, const double *rays, double M, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const double *p = rays + 5 * i;
+        orc_initial(M, p[2], p[4], p[3], p[0], p[1], out + 8 * i);
+    }
+}
+
+/* The same over given start states instead of image-plane pixels (used by
+ * the tests' conditioning checks, which trace perturbed start states):
+ * states n x 8 doubles, params n x 2 doubles (a, r_obs). out: n x ORC_REC. */
+typedef struct {
+    const double *states, *params;
+    const orc_options *o;
+    double *out;
+    int64_t begin, end;
+} orc_state_job;
+
+static void *orc_state_worker(void *arg)
+{
+    orc_state_job *j = (orc_state_job *)arg;
+    for (int64_t i = j->begin; i < j->end; ++i) {
+        double y[8];
+        memcpy(y, j->states + 8 * i, sizeof y);
+        orc_trace(j->o->M, j->params[2 * i], j->params[2 * i + 1], j->o, y, j->out + ORC_REC * i);
+    }
+    return NULL;
+}
+
+int orc_trace_states(int64_t n, const double *states, const double *params, const orc_options *o, double *out,
+                     int nthreads)
+{
+    if (n <= 0)
+        return 0;
+    if (nthreads < 1)
+        nthreads = 1;
+    if (nthreads > 1024)
+        nthreads = 1024;
+    if ((int64_t)nthreads > n)
+        nthreads = (int)n;
+    pthread_t th[1024];
+    int created[1024];
+    orc_state_job jobs[1024];
+    int64_t chunk = (n + nthreads - 1) / nthreads;
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t].states = states;
+        jobs[t].params = params;
+        jobs[t].o = o;
+        jobs[t].out = out;
+        jobs[t].begin = t * chunk < n ? t * chunk : n;
+        jobs[t].end = (t + 1) * chunk < n ? (t + 1) * chunk : n;
+        created[t] = 0;
+        if (jobs[t].begin >= jobs[t].end)
+            continue;
+        if (pthread_create(&th[t], NULL, orc_state_worker, &jobs[t]) == 0)
+            created[t] = 1;
+        else
+            orc_state_worker(&jobs[t]);
+    }
+    for (int t = 0; t < nthreads; ++t)
+        if (created[t])
+            pthread_join(th[t], NULL);
+    return 0;
+}

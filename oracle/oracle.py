@@ -90,6 +90,10 @@ def lib():
         L.orc_trace.argtypes = [d, d, d, C.POINTER(_Options), _dp, _dp]
         L.orc_trace_many.restype = C.c_int
         L.orc_trace_many.argtypes = [i64, _dp, C.POINTER(_Options), _dp, C.c_int]
+        L.orc_trace_states.restype = C.c_int
+        L.orc_trace_states.argtypes = [i64, _dp, _dp, C.POINTER(_Options), _dp, C.c_int]
+        L.orc_initial_many.restype = None
+        L.orc_initial_many.argtypes = [i64, _dp, d, _dp]
         _lib = L
     return _lib
 
@@ -227,6 +231,34 @@ def trace_many(rays, opts=None, nthreads=None):
     return out
 
 
+def initial_many(rays, M=1.0):
+    """Start states (n, 8) of the rays (alpha, beta, a, incl, r_obs)."""
+    rays = np.ascontiguousarray(np.asarray(rays, dtype=np.float64).reshape(-1, 5))
+    out = np.zeros((rays.shape[0], 8))
+    if rays.shape[0]:
+        lib().orc_initial_many(rays.shape[0], _ptr(rays), float(M), _ptr(out))
+    return out
+
+
+def trace_states(states, a, r_obs, opts=None, nthreads=None):
+    """Trace from given start states: states (n, 8); a and r_obs per ray
+    (arrays of n, or scalars).  Returns (n, 17) records as trace_many."""
+    opts = opts or Options()
+    states = np.ascontiguousarray(np.asarray(states, dtype=np.float64).reshape(-1, 8))
+    n = states.shape[0]
+    params = np.empty((n, 2))
+    params[:, 0] = a
+    params[:, 1] = r_obs
+    out = np.zeros((n, REC))
+    if n == 0:
+        return out
+    if nthreads is None:
+        nthreads = os.cpu_count() or 1
+    o = opts._c()
+    lib().orc_trace_states(n, _ptr(states), _ptr(params), C.byref(o), _ptr(out), int(nthreads))
+    return out
+
+
 def pixel_centres(nx, ny, a0, a1, b0, b1):
     """Pixel-centre grid of one image (reading: alpha_j = a0 + (j + 1/2)
     (a1 - a0)/nx, likewise beta; ray index = row * nx + column, row along
@@ -256,6 +288,6 @@ __all__ = [
     "ACTIVE", "CAPTURED", "ESCAPED", "STEP_CAP", "NONFINITE", "EQUATOR", "STEP_BENCH", "STEP_EQ2",
     "REC", "Options", "horizon", "metric", "inverse_metric", "metric_derivs",
     "christoffel", "rhs", "null_norm", "xi", "invariants", "initial", "step_size",
-    "rk4", "remap", "hermite", "stop_surface", "trace", "trace_many",
+    "rk4", "remap", "hermite", "stop_surface", "trace", "trace_many", "trace_states", "initial_many",
     "pixel_centres", "image_rays", "lib",
 ]

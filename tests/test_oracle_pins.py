@@ -363,6 +363,45 @@ def test_pole_crossing_ray_from_the_paper(orc):
     assert g["r0_sin_theta0"] < T.polar_shadow_radius(a)
 
 
+@pytest.mark.parametrize("a,r,th", [(0.9, 6.0, 1.1), (0.5, 40.0, 0.3), (0.99, 2.5, 1.6)])
+def test_euler_redo_is_one_ninth_step_from_the_old_state(orc, a, r, th):
+    """Sec. 2, text after Eq. 4: when the null condition fails by more than
+    eps after an RK4 step, the step is taken again as a forward-Euler step of
+    one ninth of its length from the state it started from.  A one-step trace
+    of a state whose k is pushed off the null cone must end exactly on
+    y + (h/9) dy/dl(y), with one redo counted and an affine length of |h|/9;
+    the same trace from the null state takes the RK4 step of full length."""
+    y = np.array([0.0, r, th, 0.3, 0.0, -0.7, 0.05, 0.02])
+    g = orc.metric(M, a, r, th)
+    # k^t the future root of g(k, k) = 0, so y starts on the null cone
+    A, B = g[0, 0], 2 * (g[0, 3] * y[7])
+    C = g[1, 1] * y[5] ** 2 + g[2, 2] * y[6] ** 2 + g[3, 3] * y[7] ** 2
+    assert A < 0  # outside the ergoregion: the larger root is the future one
+    y[4] = (-B - math.sqrt(B * B - 4 * A * C)) / (2 * A)
+    r_h = orc.horizon(M, a)
+    # the benchmark step rule written out: |h| = max(min(r/32, (r - r_h)/(2|k^r|)), 1e-3), backward
+    h = -max(min(r / 32.0, (r - r_h) / (2.0 * abs(y[5]))), 1e-3)
+    one = orc.Options(max_steps=1)
+    rec = orc.trace(a, 1000.0, y, one)
+    y_rk4, _ = orc.rk4(M, a, y, h)
+    assert rec[0] == orc.STEP_CAP and rec[1] == 1 and rec[2] == 0
+    assert np.allclose(rec[8:16], orc.remap(y_rk4)[0], rtol=0, atol=1e-15 * np.abs(y_rk4).max())
+    assert rec[16] == pytest.approx(abs(h), rel=1e-15)
+    bad = y.copy()
+    bad[5] *= 1.05  # off the null cone by ~10 %: |xi + 1| >> 1e-3
+    assert abs(orc.xi(M, a, bad) + 1.0) > 1e-2
+    h_bad = -max(min(r / 32.0, (r - r_h) / (2.0 * abs(bad[5]))), 1e-3)
+    rec = orc.trace(a, 1000.0, bad, one)
+    want = bad + (h_bad / 9.0) * orc.rhs(M, a, bad)
+    assert rec[0] == orc.STEP_CAP and rec[1] == 1 and rec[2] == 1
+    assert np.allclose(rec[8:16], orc.remap(want)[0], rtol=0, atol=1e-15 * np.abs(want).max())
+    assert rec[16] == pytest.approx(abs(h_bad) / 9.0, rel=1e-15)
+    # neither a third of the step nor a redo from the rejected RK4 end point
+    y1_bad, _ = orc.rk4(M, a, bad, h_bad)
+    for wrong in (bad + (h_bad / 3.0) * orc.rhs(M, a, bad), y1_bad + (h_bad / 9.0) * orc.rhs(M, a, y1_bad)):
+        assert np.abs(rec[8:16] - orc.remap(wrong)[0]).max() > 1e-6
+
+
 @pytest.mark.parametrize("b", [2.5, 4.0, 6.0, 9.0, 20.0])
 def test_equator_crossing_matches_schwarzschild_quadrature(orc, b):
     """Grid projection (Sec. 3): seen face-on, a Schwarzschild photon's orbit
