@@ -32,12 +32,13 @@ if ROOT not in sys.path:
 METRIC = "photon RK4 steps/s FP32 vs FP64, 1 GB300; p50/p99 image-request latency"
 UNIT = "photon-steps/s"
 
-# Algorithmic work of one accepted step of the compensated FP32 path, counted
-# on the closed-form source (FMA = 2 flops, add/mul = 1; each divide and each
-# sincos counted as 1 flop and listed apart): 4 right-hand sides x 109, stage
-# states 37, RK4 combination 41, compensated update 32, Eq. 4 monitor 39,
-# step rule 6.
-F_STEP = 591
+# Algorithmic work of one step, counted on the closed-form source (FMA = 2
+# flops, add/mul = 1; each divide and each sincos counted as 1 flop and listed
+# apart): 4 right-hand sides x 109, stage states 37, RK4 combination 41, Eq. 4
+# monitor 39, step rule 6 = 559.  The compensated (Kahan) state update adds 32
+# flops of overhead that the roofline fraction does not credit.
+F_STEP = 559
+F_KAHAN = 32
 # Special-function work per step: one full sin/cos (the step's end point), three
 # by angle addition with short series (the interior stages, no SFU), and about
 # seven SFU reciprocals (one per geometry, plain; one or two in the step size,
@@ -46,15 +47,15 @@ F_STEP = 591
 # 152 x 16 x 2.070e9 / 7 = 7.2e11 steps/s, far above the FMA bound.
 SPECIAL_PER_STEP = {"sincos_full": 1, "sincos_by_angle_addition": 3, "sfu_reciprocal": 7}
 SFU_PER_CLK_PER_SM = 16
-# FP32 non-tensor peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.070 GHz.
+# Nominal FP32 non-tensor peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x
+# 2.070 GHz (context; the roofline divides by the rate measured in the run).
 SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0
 # DRAM bytes (read + write) of one launch of the dominant kernel (the
-# single-precision pass of this workload) from an ncu capture, see
-# profiles/trace32_kernel_kerr1024_sel64_planned.md: 140,259,072 read +
-# 66,909,440 written.
+# single-precision pass of this workload) from an ncu capture of that kernel:
+# 140,259,072 read + 66,909,440 written.
 TRAFFIC_BYTES = 207168512
-# FP64 non-tensor: 2 FP64 lanes per SM on this part.
+# Nominal FP64 non-tensor peak at 2 FP64 lanes per SM (context only).
 FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1000.0
 
 
@@ -94,6 +95,11 @@ def parse_args():
     p.add_argument("--ring-out", default="", help="rings workload: write the per-image table here (JSON)")
     p.add_argument("--frame-steps", type=int, default=8, help="view workload: RK4 steps per frame")
     p.add_argument("--frame-out", default="", help="view workload: write one frame here (PGM)")
+    p.add_argument("--no-serve", action="store_true", help="skip the serving leg of the default workload")
+    p.add_argument("--serve-rates", default="10,30", help="serving leg: Poisson arrival rates (req/s)")
+    p.add_argument("--serve-seconds", type=float, default=20.0, help="serving leg: seconds of arrivals per rate")
+    p.add_argument("--serve-saturation", type=int, default=80,
+                   help="serving leg: requests offered at once to measure the saturated rate (0: skip)")
     return p.parse_args()
 
 
@@ -143,6 +149,40 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows),
                 "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()), default=None)}
+
+
+# ------------------------------------------------------ measured ALU peaks ---
+
+def measure_alu_peaks(gray, torch, launches=24):
+    """Non-tensor FP32 and FP64 FMA rates of this device from the library's
+    FMA-chain microbenchmark (gray_fma_peak: 8 independent chains per thread,
+    every SM filled with 2048 threads), timed with CUDA events on the
+    launching stream, with the SM clock sampled while it runs.  Changes no
+    GPU setting."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks, threads = sms * 8, 256
+    stream = torch.cuda.current_stream()
+    out = {"sms": sms, "blocks": blocks, "threads": threads, "chains_per_thread": 8}
+    for name, prec, iters, dt in (("fp32", gray.FP32, 1 << 17, torch.float32),
+                                  ("fp64", gray.FP64, 1 << 11, torch.float64)):
+        sink = torch.empty(blocks * threads, dtype=dt, device="cuda")
+        gray.gray_fma_peak(prec, blocks, threads, iters, sink)  # warm-up
+        torch.cuda.synchronize()
+        clk = ClockSampler(torch.cuda.current_device())
+        clk.start()
+        time.sleep(0.25)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(launches)]
+        flop = 0
+        for a, b in ev:
+            a.record(stream)
+            flop = gray.gray_fma_peak(prec, blocks, threads, iters, sink)
+            b.record(stream)
+        torch.cuda.synchronize()
+        c = clk.stop()
+        ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        out[name] = {"tflops": flop / (ms / 1000.0) / 1e12, "ms_per_launch": ms, "flop_per_launch": flop,
+                     "sm_mhz": c.get("sm_mhz"), "sm_max_mhz": c.get("sm_max_mhz"), "reasons": c.get("reasons")}
+    return out
 
 
 # ------------------------------------------------------------- CPU oracle ---
@@ -334,6 +374,33 @@ def run_serve(args):
         out.append(summ)
         print(json.dumps({"workload": "serve", "rate": rate, **summ}), flush=True)
     return 0
+
+
+def serving_leg(args, rates, seconds, saturation):
+    """Serving (the request loop of serve.py): Poisson arrivals of render
+    requests (side uniform over {32, ..., 2048}, a ~ U[0, 0.999], i ~ U[0, 90]
+    deg, r_obs = 1000, compensated FP32 + zone) at each rate for `seconds` of
+    arrivals, then `saturation` requests offered at once.  p50/p99 latency
+    (arrival to image in host memory) and photon-steps/s per rate."""
+    from paper_1303_5057_gb300 import gray, serve
+    from paper_1303_5057_gb300 import inputs as I
+    opt = gray.Options(precision=gray.FP32_KAHAN_SEL64, max_steps=10000, r_sw=args.r_sw)
+    srv = serve.Server(opt, capacity=16 << 20, round_budget=256)
+    srv.run(I.request_stream(100.0, 6, seed_index=40), realtime=False)  # warm-up
+    out = {"sides": "uniform over {32, 64, ..., 2048}", "pool_rays": 16 << 20, "round_budget": 256,
+           "precision": "fp32_kahan_sel64", "latency": "arrival to image in pinned host memory", "rates": []}
+    for rate in rates:
+        n_req = max(10, int(rate * seconds))
+        st = srv.run(I.request_stream(rate, n_req), realtime=True, max_wall=seconds * 4 + 30.0)
+        summ = st.summary()
+        summ["rate_req_per_s"] = rate
+        summ["offered"] = n_req
+        out["rates"].append(summ)
+    if saturation > 0:
+        st = srv.run(I.request_stream(1000.0, saturation, seed_index=41), realtime=False)
+        out["saturated"] = {**st.summary(), "offered_at_once": saturation}
+    srv.close()
+    return out
 
 
 def run_projection(args):
@@ -621,23 +688,47 @@ def main():
             e2e_ms.append(1000.0 * (time.perf_counter() - t0))
     e2e_value = steps_per_pass / (statistics.mean(e2e_ms) / 1000.0) * world
 
-    # ---- plain FP64 GPU path on the same image (the speed reference) ----
+    # ---- measured non-tensor FMA peaks (the roofline's denominators) ----
+    peaks = measure_alu_peaks(gray, torch) if rank == 0 else None
+    fp32_peak = peaks["fp32"]["tflops"] if peaks else FP32_PEAK_TFLOPS
+    fp64_peak = peaks["fp64"]["tflops"] if peaks else FP64_PEAK_TFLOPS
+
+    # ---- plain FP64 GPU path on the same image (the speed reference), with
+    # the same planned queue as the single-precision arm ----
     fp64 = None
     if not args.no_fp64_leg and rank == 0:
         tr64 = gray.Tracer(gray.Options(precision=gray.FP64, max_steps=10000, step_rule=rule), n)
-        tr64.setup([im])
+        order64 = torch.empty(n, dtype=torch.int32, device="cuda")
+
+        def plan64():
+            if args.no_plan:
+                tr64.setup([im])
+                return None
+            return tr64.setup_plan([im], probe_stride=args.probe_stride, probe_budget=args.probe_budget,
+                                   order=order64)
+        q = plan64()
+        tr64.trace(order=q)
+        q = plan64()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        tr64.trace(wait=False)
+        tr64.trace(wait=False, order=q)
         b.record(stream)
         torch.cuda.synchronize()
         ms64 = a.elapsed_time(b)
-        tr64.setup([im])
-        _, _, st64 = tr64.trace()
+        q = plan64()
+        _, _, st64 = tr64.trace(order=q)
         tr64.close()
         fp64 = {"value": st64[0] / (ms64 / 1000.0), "unit": UNIT, "trace_ms": ms64,
-                "roofline_frac_fp64": F_STEP * st64[0] / (ms64 / 1000.0) / 1e12 / FP64_PEAK_TFLOPS}
+                "queue": "natural" if args.no_plan else "planned (same probes as the single-precision arm)",
+                "roofline_frac_fp64": F_STEP * st64[0] / (ms64 / 1000.0) / 1e12 / fp64_peak,
+                "peak_tflops": fp64_peak, "peak_source": "measured FMA chain (gray_fma_peak)" if peaks else
+                "nominal"}
+
+    serving = None
+    if not args.no_serve and rank == 0:
+        serving = serving_leg(args, [float(x) for x in args.serve_rates.split(",") if x],
+                              args.serve_seconds, args.serve_saturation)
 
     cpu = None
     if not args.no_cpu and rank == 0:
@@ -661,14 +752,19 @@ def main():
             "ns_per_photon_step": 1e9 / (value / world),
             "steps_per_pass": steps_per_pass, "fp64_steps_per_pass": fp64_steps,
             "setup_plan_ms": statistics.mean(setup_plan_ms), "trace_ms": statistics.mean(trace_ms),
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": achieved / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": achieved / fp32_peak, "traffic": TRAFFIC_BYTES,
                          "kernel": "trace32_kernel (single-precision pass)", "kernel_ms": main_ms,
                          "kernel_steps": main_pass_steps,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (FP32 non-tensor, max clock)",
+                         "peak_source": ("measured: FP32 FMA chains (gray_fma_peak) in this run, at the SM clock in "
+                                         "measured_peaks" if peaks else "nominal 152 x 128 x 2 x 2.070 GHz"),
+                         "peak_nominal": FP32_PEAK_TFLOPS,
+                         "frac_with_kahan_update": achieved * (F_STEP + F_KAHAN) / F_STEP / fp32_peak,
                          "sfu_bound_steps_per_s": SMS * SFU_PER_CLK_PER_SM * SM_MAX_GHZ * 1e9
                          / SPECIAL_PER_STEP["sfu_reciprocal"],
-                         "flop_per_step": F_STEP, "special_per_step": SPECIAL_PER_STEP},
+                         "flop_per_step": F_STEP, "flop_per_step_with_kahan_update": F_STEP + F_KAHAN,
+                         "special_per_step": SPECIAL_PER_STEP},
+            "measured_peaks": peaks,
             "passes_ms": {"single": main_ms, "zone": zone_ms, "probe": probe_ms,
                           "zone_steps": zone_steps, "setup_plan_trace_render": total_ms / args.steps},
             "cpu_baseline": cpu,
@@ -676,6 +772,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clocks,
             "fp64_gpu": fp64,
+            "serving": serving,
             "speedup_vs_fp64_gpu": (value / world) / fp64["value"] if fp64 else None,
         }
         print(json.dumps(line), flush=True)

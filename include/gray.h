@@ -76,6 +76,13 @@ extern "C" {
 #define GRAY_EVAL_RECIP 5       /* in (x) -> out 1/x as the tracer evaluates it: refined (step rule, */
                                 /* double everywhere) and, second, the single-precision geometry's  */
                                 /* hardware approximation; 2 values                                 */
+#define GRAY_EVAL_SINCOS_DS 6   /* in (theta) -> out (sin, cos) of the float theta in the double-single */
+                                /* arithmetic of the ambiguous Eq. 4 test (GRAY_FP32 only); 2 values */
+#define GRAY_EVAL_NORM 7        /* in (M, a, y[8]) -> out, for the compensated single-precision pair */
+                                /* of y (GRAY_FP32 only): g(k, k) in double-single, g(k, k) and the  */
+                                /* size of its terms as the single-precision test evaluates them, the */
+                                /* test's ambiguity flag (1/0), its decision (1: redo), and the       */
+                                /* decision after the double-single re-test; 6 values                */
 
 /* ---- launch of the trace kernel ------------------------------------- */
 #define GRAY_LAUNCH_PERSISTENT 0     /* persistent warps refilled from a work queue (default) */
@@ -285,6 +292,17 @@ int gray_count_active(gray_ctx *ctx, const void *state_dev, size_t state_bytes, 
                       const int64_t *ranges_host, int32_t n_ranges, int64_t *counts_host,
                       void *stream);
 
+/* Asynchronous per-range statistics for resident pools, with every buffer in
+ * device memory: ranges_dev holds n_ranges (first_ray, count) int64 pairs;
+ * out_dev receives, per range, two int64: the number of ACTIVE rays and the
+ * steps its rays have taken so far (empty slots count none).  Ranges are
+ * clipped to the buffer.  Nothing waits and nothing is allocated, so a
+ * serving loop can enqueue it after each trace round and read the counts
+ * back with its own copy and event.  Errors: GRAY_EINVAL (NULL context,
+ * state too small, n_ranges < 0, NULL buffers), GRAY_ECUDA. */
+int gray_range_stats(gray_ctx *ctx, const void *state_dev, size_t state_bytes, int64_t n_state,
+                     const int64_t *ranges_dev, int32_t n_ranges, int64_t *out_dev, void *stream);
+
 /* Shadow of each of n_images images whose rays start at first_ray (as laid
  * down by gray_setup with the same image list): captured count, area of the
  * captured pixels on the image plane, equivalent radius sqrt(area/pi) and
@@ -417,6 +435,22 @@ int gray_setup_noalloc(int32_t precision, const gray_image *images_host, int32_t
  * Errors: GRAY_EINVAL, GRAY_ECUDA. */
 int gray_eval(int32_t what, int32_t precision, const double *in_dev, int64_t n,
               double *out_dev, void *stream);
+
+/* FMA-chain microbenchmark of the non-tensor FMA rate, the bound of the
+ * tracer's arithmetic (the paper states its single-precision throughput
+ * against the GPU's peak arithmetic rate: abstract, Sec. 3; this measures
+ * that peak, in FP32 and FP64, on the running device instead of deriving it
+ * from unit counts).  Launches
+ * `blocks` blocks of `threads` threads (a multiple of 32, at most 1024) on
+ * `stream`; every thread runs `iters` (a positive multiple of 8) iterations
+ * of 8 independent FMA chains in `precision` (GRAY_FP32 or GRAY_FP64) and
+ * writes one value to sink_dev (blocks x threads elements of that type,
+ * caller-owned).  One launch performs exactly
+ * 2 x 8 x iters x blocks x threads floating-point operations; the caller
+ * times it (CUDA events on the same stream).  Asynchronous.
+ * Errors: GRAY_EINVAL (precision, shape, iters, sink too small), GRAY_ECUDA. */
+int gray_fma_peak(int32_t precision, int32_t blocks, int32_t threads, int64_t iters, void *sink_dev,
+                  size_t sink_bytes, void *stream);
 
 /* Record CUDA events around the passes of every later gray_trace and
  * gray_plan call of this context (on = 1) or stop (on = 0).  Diagnostic.

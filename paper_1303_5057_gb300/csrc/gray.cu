@@ -48,7 +48,8 @@ __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_
 //   K  momentum (k^t, k^r, k^th, k^ph)  float4 / d4
 //   CX, CK  Kahan compensations         float4 (FP32 modes only)
 //   F  final position on the stop surface  float4 / d4
-//   P  per-ray constants (a, M, r_obs, 0)  d4
+//   P  per-ray constants (a, M, r_obs, w)  d4; w holds the low words of a and M as
+//      two floats (a = (float)a + a_lo, likewise M)
 //   PF0, PF1 the same constants for single precision: (a, M, r_+ hi, r_+ lo),
 //           (r_-, dc, r_h, r_obs)  float4 each (FP32 modes only)
 //   S0 (status, steps, Euler redos, pole remaps)  int4
@@ -180,6 +181,7 @@ struct gray_ctx {
     bool ev_used[3] = {false, false, false};
     cudaStream_t side = nullptr;       // gray_setup_plan: the planning passes (high priority)
     cudaEvent_t fork = nullptr, join = nullptr;
+    float4 *sincos_table = nullptr;    // device: the double-single Eq. 4 re-test's table (8 KB)
 };
 
 namespace {
@@ -249,7 +251,13 @@ __device__ void store_initial(const StateView &v, int prec, int64_t i, const dou
         v.PF0[i] = make_float4(c8[0], c8[1], c8[2], c8[3]);
         v.PF1[i] = make_float4(c8[4], c8[5], c8[6], c8[7]);
     }
-    st_d4(v.P, i, a, M, r_obs, 0.0);
+    // the fourth slot of P holds the low words of a and M as two floats
+    // (a = (float)a + a_lo): the double-single Eq. 4 test needs them
+    const float a_hi = (float)a, M_hi = (float)M;
+    const float2 low = make_float2((float)(a - (double)a_hi), (float)(M - (double)M_hi));
+    double w;
+    memcpy(&w, &low, sizeof w);
+    st_d4(v.P, i, a, M, r_obs, w);
     v.S0[i] = make_int4(GRAY_RAY_ACTIVE, 0, 0, 0);
     v.S1[i] = make_int4(0, 0, 0, 0);
 }
@@ -363,7 +371,8 @@ __device__ __forceinline__ double ninth(double h) { return h * (1.0 / 9.0); }
 // the stop surfaces are interpolated by stop_surface_mixed.
 template <typename T, bool KAHAN, bool MIXED_STOP = false>
 __device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, T *y, T *c, Geo<T> &g, T *fin,
-                                         int &euler, int &remaps)
+                                         int &euler, int &remaps, const float2 *aM_lo = nullptr,
+                                         const float4 *sincos_table = nullptr)
 {
     T h = step_size(H, O, y);
     T a1[4], a2[4], a3[4], a4[4];
@@ -396,7 +405,22 @@ __device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, 
     Geo<T> g1 = geometry(H, y1[1], y1[2], KAHAN ? -c1[1] : T(0), KAHAN ? -c1[2] : T(0));
 
     // Eq. 4 monitor: redo the step as forward Euler at h/9 when |xi + 1| > eps.
-    if (xi_fails(H, g1, y1, O.eps_xi)) {
+    // Compensated single precision: a test whose outcome lies within its own
+    // rounding is taken again in double-single arithmetic on the compensated
+    // state, with the ray's spin and mass split into two floats (aM), so the
+    // decision follows the one the double method takes at that state.
+    bool redo;
+    if constexpr (sizeof(T) == 4 && KAHAN) {
+        bool ambiguous;
+        redo = xi_fails_flag(H, g1, y1, O.eps_xi, ambiguous);
+        if (ambiguous && aM_lo && sincos_table) {
+            const float2 lo = *aM_lo;
+            redo = xi_fails_ds(y1, c1, make_float4(H.a, lo.x, H.M, lo.y), sincos_table, O.eps_xi);
+        }
+    } else {
+        redo = xi_fails(H, g1, y1, O.eps_xi);
+    }
+    if (redo) {
         h = ninth(h);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
@@ -488,6 +512,7 @@ struct TraceArgs {
     int zone_return;    // zone pass: a ray climbing out of the zone goes to the return list
     double h_frac, h_min, eps_xi, cap_frac, r_esc_frac, r_sw;
     Workspace *ws;
+    const float4 *sincos_table; // the double-single Eq. 4 re-test's sin/cos table
 };
 
 template <int MODE> struct ModeTraits {
@@ -564,6 +589,7 @@ template <int MODE> __global__ void __maxnreg__(128) trace32_kernel(TraceArgs A)
     O.h_frac = (float)A.h_frac;
     O.h_min = (float)A.h_min;
     O.eps_xi = (float)A.eps_xi;
+    O.eps_xi_d = A.eps_xi;
     O.step_rule = A.step_rule;
     O.stop_equator = A.stop_equator;
 
@@ -680,7 +706,8 @@ template <int MODE> __global__ void __maxnreg__(128) trace32_kernel(TraceArgs A)
                         handoff = true;
                     }
                 } else {
-                    status = step_once<float, KAHAN>(H, O, y, c, geo, fin, euler, remaps);
+                    status = step_once<float, KAHAN>(H, O, y, c, geo, fin, euler, remaps, (const float2 *)&v.P[id].w,
+                                                     A.sincos_table);
                     ++steps;
                 }
                 if (status != GRAY_RAY_ACTIVE || yield || handoff) {
@@ -715,6 +742,7 @@ __global__ void __launch_bounds__(128) trace64_kernel(TraceArgs A)
     O.h_frac = A.h_frac;
     O.h_min = A.h_min;
     O.eps_xi = A.eps_xi;
+    O.eps_xi_d = A.eps_xi;
     O.step_rule = A.step_rule;
     O.stop_equator = A.stop_equator;
 
@@ -825,12 +853,14 @@ __global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
     Od.h_frac = A.h_frac;
     Od.h_min = A.h_min;
     Od.eps_xi = A.eps_xi;
+    Od.eps_xi_d = A.eps_xi;
     Od.step_rule = A.step_rule;
     Od.stop_equator = A.stop_equator;
     StepOpt<float> Of;
     Of.h_frac = (float)A.h_frac;
     Of.h_min = (float)A.h_min;
     Of.eps_xi = (float)A.eps_xi;
+    Of.eps_xi_d = A.eps_xi;
     Of.step_rule = A.step_rule;
     Of.stop_equator = A.stop_equator;
     const int64_t n = (int64_t)*(volatile unsigned long long *)&A.ws->handoff;
@@ -959,7 +989,8 @@ __global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
                         ++n64;
                         ++tot_fp64;
                     } else {
-                        status = step_once<float, true>(Hf, Of, yf, cf, gf, finf, euler, remaps);
+                        status = step_once<float, true>(Hf, Of, yf, cf, gf, finf, euler, remaps, (const float2 *)&v.P[id].w,
+                                                     A.sincos_table);
                         for (int m = 0; m < 4; ++m)
                             find[m] = finf[m];
                     }
@@ -1018,24 +1049,44 @@ __global__ void clear_kernel(StateView v, int64_t first, int64_t n)
 }
 
 // ACTIVE rays of each range (first, count): one block per range.
-__global__ void count_ranges_kernel(const int4 *S0, const long long *ranges, unsigned long long *counts)
+// Per range of rays (one block each): the number of ACTIVE rays and the
+// steps all of them have taken, written to out[2 k] and out[2 k + 1].  A
+// range is clipped to the buffer [0, n) (ranges may live in device memory,
+// where the host cannot check them).
+__global__ void range_stats_kernel(const int4 *S0, int64_t n, const long long *ranges, unsigned long long *out)
 {
-    const long long first = ranges[2 * blockIdx.x], len = ranges[2 * blockIdx.x + 1];
-    unsigned long long mine = 0;
-    for (long long i = threadIdx.x; i < len; i += blockDim.x)
-        mine += (S0[first + i].x == GRAY_RAY_ACTIVE);
+    long long first = ranges[2 * blockIdx.x], len = ranges[2 * blockIdx.x + 1];
+    if (first < 0) {
+        len += first;
+        first = 0;
+    }
+    if (len > n - first)
+        len = n - first;
+    unsigned long long act = 0, steps = 0;
+    for (long long i = threadIdx.x; i < len; i += blockDim.x) {
+        const int4 s0 = S0[first + i];
+        act += (s0.x == GRAY_RAY_ACTIVE);
+        steps += (unsigned long long)(s0.x == GRAY_RAY_EMPTY ? 0 : s0.y);
+    }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
-        mine += __shfl_xor_sync(0xffffffffu, mine, off);
-    __shared__ unsigned long long part[32];
-    if ((threadIdx.x & 31) == 0)
-        part[threadIdx.x >> 5] = mine;
+    for (int off = 16; off > 0; off >>= 1) {
+        act += __shfl_xor_sync(0xffffffffu, act, off);
+        steps += __shfl_xor_sync(0xffffffffu, steps, off);
+    }
+    __shared__ unsigned long long part[2][32];
+    if ((threadIdx.x & 31) == 0) {
+        part[0][threadIdx.x >> 5] = act;
+        part[1][threadIdx.x >> 5] = steps;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-            t += part[w];
-        counts[blockIdx.x] = t;
+        unsigned long long t = 0, u = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t += part[0][w];
+            u += part[1][w];
+        }
+        out[2 * blockIdx.x] = t;
+        out[2 * blockIdx.x + 1] = u;
     }
 }
 
@@ -1613,11 +1664,26 @@ __global__ void splat_kernel(StateView v, int prec, int64_t first, int64_t n, Ca
     deposit<T>(c, px, py, z, count, depth);
 }
 
+// The sin/cos table of the double-single Eq. 4 re-test: sin and cos of j/32,
+// j in [-256, 256), each as the two floats nearest to the double value and
+// to its remainder (computed in double, ~2^-48 relative after the split).
+__global__ void sincos_table_kernel(float4 *table)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2 * SINCOS_TABLE_HALF)
+        return;
+    double s, c;
+    sincos((double)(k - SINCOS_TABLE_HALF) * 0.03125, &s, &c);
+    const float sh = (float)s, ch = (float)c;
+    table[k] = make_float4(sh, (float)(s - (double)sh), ch, (float)(c - (double)ch));
+}
+
 // --------------------------------------------------------------------------
 // Unit evaluations for parity tests
 // --------------------------------------------------------------------------
 
-template <typename T> __global__ void eval_kernel(int what, const double *in, int64_t n, double *out)
+template <typename T>
+__global__ void eval_kernel(int what, const double *in, int64_t n, double *out, const float4 *sincos_table)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
@@ -1655,6 +1721,41 @@ template <typename T> __global__ void eval_kernel(int what, const double *in, in
     } else if (what == GRAY_EVAL_RECIP) {
         out[2 * i] = (double)recip((T)in[i]);
         out[2 * i + 1] = (double)recip_approx((T)in[i]);
+    } else if (what == GRAY_EVAL_SINCOS_DS) {
+        if constexpr (sizeof(T) == 4) {
+            ds sv, cv;
+            ds_sincos((float)in[i], sincos_table, sv, cv);
+            out[2 * i] = (double)sv.hi + (double)sv.lo;
+            out[2 * i + 1] = (double)cv.hi + (double)cv.lo;
+        }
+    } else if (what == GRAY_EVAL_NORM) {
+        if constexpr (sizeof(T) == 4) {
+            const double *q = in + 10 * i;
+            const double M = q[0], a = q[1];
+            float y1[8], c1[8];
+            for (int m = 0; m < 8; ++m) {
+                y1[m] = (float)q[2 + m];
+                c1[m] = (float)((double)y1[m] - q[2 + m]);
+            }
+            float c8[8];
+            hole_constants_f(a, M, 1000.0, c8);
+            const Hole<float> H = make_hole_f(make_float4(c8[0], c8[1], c8[2], c8[3]),
+                                              make_float4(c8[4], c8[5], c8[6], c8[7]), 1.0f, 1.0f, 0.0f);
+            const Geo<float> g = geometry(H, y1[1], y1[2], -c1[1], -c1[2]);
+            const float eps = 1e-3f;
+            bool amb;
+            const bool redo = xi_fails_flag(H, g, y1, eps, amb);
+            const NormF nf = null_norm_f(H, g, y1);
+            const float4 aM = make_float4(H.a, (float)(a - (double)(float)a), H.M, (float)(M - (double)(float)M));
+            float iS;
+            const ds nd = null_norm_ds(y1, c1, aM, sincos_table, iS);
+            out[6 * i] = (double)nd.hi + (double)nd.lo;
+            out[6 * i + 1] = (double)nf.norm;
+            out[6 * i + 2] = (double)nf.size;
+            out[6 * i + 3] = amb ? 1.0 : 0.0;
+            out[6 * i + 4] = redo ? 1.0 : 0.0;
+            out[6 * i + 5] = xi_fails_ds(y1, c1, aM, sincos_table, eps) ? 1.0 : 0.0;
+        }
     } else if (what == GRAY_EVAL_XI) {
         const double *q = in + 10 * i;
         const Hole<T> H = cast_hole<T>(make_hole(q[1], q[0], 1.0, 1.0, 1.0, 0.0));
@@ -1663,6 +1764,41 @@ template <typename T> __global__ void eval_kernel(int what, const double *in, in
             y[m] = (T)q[2 + m];
         out[i] = (double)xi_eq4<T>(H, y);
     }
+}
+
+// --------------------------------------------------------------------------
+// FMA-chain microbenchmark: the non-tensor FP32 / FP64 FMA rate that bounds
+// the tracer (the denominators of its roofline), measured rather than taken
+// from unit counts.  Each thread runs PEAK_CHAINS independent chains
+// x <- x * m + b (contracting towards b / (1 - m), so nothing overflows);
+// the chains hide the FMA latency and the sums go to a sink so the compiler
+// keeps every FMA.
+// --------------------------------------------------------------------------
+
+constexpr int PEAK_CHAINS = 8;
+
+template <typename T> __global__ void fma_peak_kernel(int64_t iters, T *sink)
+{
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const T m = T(0.9999995), b = T(1e-7);
+    T x[PEAK_CHAINS];
+#pragma unroll
+    for (int j = 0; j < PEAK_CHAINS; ++j)
+        x[j] = T(1) + T(j) * T(1e-3) + T(threadIdx.x) * T(1e-6);
+#pragma unroll 1
+    for (int64_t i = 0; i < iters; i += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+#pragma unroll
+            for (int j = 0; j < PEAK_CHAINS; ++j)
+                x[j] = fma(x[j], m, b);
+        }
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < PEAK_CHAINS; ++j)
+        acc += x[j];
+    sink[tid] = acc;
 }
 
 // --------------------------------------------------------------------------
@@ -1868,6 +2004,17 @@ int gray_create(gray_ctx **ctx, const gray_options *opt)
         gray_destroy(c);
         return GRAY_ECUDA;
     }
+    if (cudaMalloc((void **)&c->sincos_table, 2 * SINCOS_TABLE_HALF * sizeof(float4)) != cudaSuccess) {
+        gray_destroy(c);
+        return GRAY_ENOMEM;
+    }
+    // filled once, on the legacy stream, and waited for: every later call of
+    // the context (on any stream, or captured in a graph) finds it ready
+    sincos_table_kernel<<<2 * SINCOS_TABLE_HALF / 128, 128>>>(c->sincos_table);
+    if (check_launch() != GRAY_OK || cudaStreamSynchronize(0) != cudaSuccess) {
+        gray_destroy(c);
+        return GRAY_ECUDA;
+    }
     std::memset(c->ws_host, 0, sizeof(Workspace));
     *ctx = c;
     return GRAY_OK;
@@ -1888,6 +2035,7 @@ void gray_destroy(gray_ctx *ctx)
         cudaStreamDestroy(ctx->side);
     cudaFree(ctx->ws);
     cudaFree(ctx->aux);
+    cudaFree(ctx->sincos_table);
     cudaFreeHost(ctx->ws_host);
     delete ctx;
 }
@@ -1964,6 +2112,7 @@ TraceArgs make_trace_args(gray_ctx *ctx, void *state, int64_t n_state, int64_t s
     A.r_esc_frac = o.r_esc_frac;
     A.r_sw = o.r_sw;
     A.ws = ctx->ws;
+    A.sincos_table = ctx->sincos_table;
     A.one_per_thread = o.launch == GRAY_LAUNCH_ONE_PER_THREAD;
     A.stop_equator = o.stop_equator;
     A.zone_return = 0;
@@ -2356,20 +2505,38 @@ int gray_count_active(gray_ctx *ctx, const void *state, size_t state_bytes, int6
     void *dr = nullptr, *dc = nullptr;
     if ((rc = upload_table(ranges, 2 * sizeof(int64_t) * (size_t)n_ranges, s, &dr)))
         return rc;
-    if (cudaMallocAsync(&dc, sizeof(unsigned long long) * (size_t)n_ranges, s) != cudaSuccess) {
+    if (cudaMallocAsync(&dc, 2 * sizeof(unsigned long long) * (size_t)n_ranges, s) != cudaSuccess) {
         cudaFreeAsync(dr, s);
         return GRAY_ECUDA;
     }
     StateView v = make_view((void *)state, n_state, ctx->opt.precision);
-    count_ranges_kernel<<<(unsigned)n_ranges, 256, 0, s>>>(v.S0, (const long long *)dr, (unsigned long long *)dc);
+    range_stats_kernel<<<(unsigned)n_ranges, 256, 0, s>>>(v.S0, n_state, (const long long *)dr,
+                                                          (unsigned long long *)dc);
     rc = check_launch();
-    if (!rc && cudaMemcpyAsync(counts, dc, sizeof(int64_t) * (size_t)n_ranges, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (!rc && cudaMemcpy2DAsync(counts, sizeof(int64_t), dc, 2 * sizeof(int64_t), sizeof(int64_t), (size_t)n_ranges,
+                                 cudaMemcpyDeviceToHost, s) != cudaSuccess)
         rc = GRAY_ECUDA;
     cudaFreeAsync(dr, s);
     cudaFreeAsync(dc, s);
     if (!rc && cudaStreamSynchronize(s) != cudaSuccess)
         rc = GRAY_ECUDA;
     return rc;
+}
+
+int gray_range_stats(gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_state, const int64_t *ranges,
+                     int32_t n_ranges, int64_t *out, void *stream)
+{
+    int rc = check_state(ctx, state, state_bytes, n_state);
+    if (rc)
+        return rc;
+    if (n_ranges < 0 || (n_ranges > 0 && (!ranges || !out)))
+        return GRAY_EINVAL;
+    if (n_ranges == 0)
+        return GRAY_OK;
+    StateView v = make_view((void *)state, n_state, ctx->opt.precision);
+    range_stats_kernel<<<(unsigned)n_ranges, 256, 0, (cudaStream_t)stream>>>(v.S0, n_state, (const long long *)ranges,
+                                                                             (unsigned long long *)out);
+    return check_launch();
 }
 
 int gray_render(gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_state, int64_t first_ray, int64_t n,
@@ -2566,19 +2733,49 @@ int gray_splat(gray_ctx *ctx, const void *state, size_t state_bytes, int64_t n_s
 
 int gray_eval(int32_t what, int32_t precision, const double *in, int64_t n, double *out, void *stream)
 {
-    if (what < GRAY_EVAL_CHRISTOFFEL || what > GRAY_EVAL_RECIP || n < 0)
+    if (what < GRAY_EVAL_CHRISTOFFEL || what > GRAY_EVAL_NORM || n < 0)
         return GRAY_EINVAL;
     if (precision != GRAY_FP64 && precision != GRAY_FP32)
         return GRAY_EINVAL;
+    if (what >= GRAY_EVAL_SINCOS_DS && precision != GRAY_FP32)
+        return GRAY_EINVAL; // the double-single evaluations exist in single precision only
     if (n == 0)
         return GRAY_OK;
     if (!in || !out)
         return GRAY_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
+    if (precision == GRAY_FP64) {
+        eval_kernel<double><<<grid_for(n, 128), 128, 0, s>>>(what, in, n, out, nullptr);
+        return check_launch();
+    }
+    float4 *table = nullptr;
+    if (cudaMallocAsync((void **)&table, 2 * SINCOS_TABLE_HALF * sizeof(float4), s) != cudaSuccess)
+        return GRAY_ECUDA;
+    sincos_table_kernel<<<2 * SINCOS_TABLE_HALF / 128, 128, 0, s>>>(table);
+    int rc = check_launch();
+    if (!rc) {
+        eval_kernel<float><<<grid_for(n, 128), 128, 0, s>>>(what, in, n, out, table);
+        rc = check_launch();
+    }
+    cudaFreeAsync(table, s);
+    return rc;
+}
+
+int gray_fma_peak(int32_t precision, int32_t blocks, int32_t threads, int64_t iters, void *sink, size_t sink_bytes,
+                  void *stream)
+{
+    if (precision != GRAY_FP64 && precision != GRAY_FP32)
+        return GRAY_EINVAL;
+    if (blocks < 1 || threads < 32 || threads > 1024 || threads % 32 != 0 || iters < 8 || iters % 8 != 0)
+        return GRAY_EINVAL;
+    const size_t per = precision == GRAY_FP64 ? sizeof(double) : sizeof(float);
+    if (!sink || sink_bytes < per * (size_t)blocks * (size_t)threads)
+        return GRAY_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
     if (precision == GRAY_FP64)
-        eval_kernel<double><<<grid_for(n, 128), 128, 0, s>>>(what, in, n, out);
+        fma_peak_kernel<double><<<blocks, threads, 0, s>>>(iters, (double *)sink);
     else
-        eval_kernel<float><<<grid_for(n, 128), 128, 0, s>>>(what, in, n, out);
+        fma_peak_kernel<float><<<blocks, threads, 0, s>>>(iters, (float *)sink);
     return check_launch();
 }
 
@@ -2598,7 +2795,9 @@ int gray_setup_noalloc(int32_t precision, const gray_image *images, int32_t n_im
 {
     if (precision < GRAY_FP64 || precision > GRAY_FP32_KAHAN_SEL64)
         return GRAY_EINVAL;
-    if (!images || n_images < 1 || n_images > GRAY_NOALLOC_MAX_IMAGES || !state || n_state < 0 || first_ray < 0)
+    // ray indices are 32-bit in the work queues, as in gray_setup
+    if (!images || n_images < 1 || n_images > GRAY_NOALLOC_MAX_IMAGES || !state || n_state < 0 ||
+        n_state > 0x7fffffff || first_ray < 0)
         return GRAY_EINVAL;
     if (state_bytes < gray_state_bytes(n_state, precision))
         return GRAY_EINVAL;

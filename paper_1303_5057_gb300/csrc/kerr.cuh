@@ -64,6 +64,7 @@ template <typename T> struct Hole {
 // Integration options used inside a step.
 template <typename T> struct StepOpt {
     T h_frac, h_min, eps_xi;
+    double eps_xi_d;  // eps_xi in double, for the double confirmation of ambiguous single-precision tests
     int step_rule;    // 0: benchmark rule, 1: Eq. 2
     int stop_equator; // 1: stop at the first crossing of theta = pi/2 (Sec. 3 projection)
 };
@@ -436,6 +437,158 @@ template <typename T> __device__ __forceinline__ bool xi_fails(const Hole<T> &H,
     const T norm = fma(g.Sigma, fma(kr * g.iD, kr, kh * kh), E * g.iS);
     const T den = fma(H.m2M * r, g.iS, T(1)) * (kt * kt);
     return !(fabs(norm) <= eps * fabs(den));
+}
+
+// The null norm g(k, k) of the single-precision Eq. 4 test, in the metric's
+// Carter-frame form, with the size of the terms that make it up (the sum of
+// their magnitudes) and g_tt (k^t)^2.
+struct NormF {
+    float norm, size, den;
+};
+__device__ __forceinline__ NormF null_norm_f(const Hole<float> &H, const Geo<float> &g, const float *y)
+{
+    const float r = g.r, s2 = g.s * g.s;
+    const float kt = y[4], kr = y[5], kh = y[6], kp = y[7];
+    const float w = fmaf(-(H.a * s2), kp, kt);
+    const float v = fmaf(fmaf(r, r, H.a2), kp, -(H.a * kt));
+    const float sv2 = (s2 * v) * v, dw2 = (g.Delta * w) * w;
+    const float q = fmaf(kr * g.iD, kr, kh * kh);
+    NormF o;
+    o.norm = fmaf(g.Sigma, q, (sv2 - dw2) * g.iS);
+    o.size = fmaf(g.Sigma, fabsf(q), (sv2 + fabsf(dw2)) * g.iS);
+    o.den = fmaf(H.m2M * r, g.iS, 1.0f) * (kt * kt);
+    return o;
+}
+
+// The single-precision Eq. 4 test, with a flag set when its outcome lies
+// within the rounding of its own evaluation: |g(k, k)| and the threshold
+// eps |g_tt (k^t)^2| closer than 2^-20 of the size of the terms that make up
+// g(k, k).  Single precision evaluates g(k, k) to a few units of 2^-24 of
+// that size (the geometry's reciprocal and sin/cos to 2-4 ulp, the high words
+// of k to 2^-24 relative); such a test is taken again in double-single
+// arithmetic (xi_fails_ds).
+__device__ __forceinline__ bool xi_fails_flag(const Hole<float> &H, const Geo<float> &g, const float *y, float eps,
+                                              bool &ambiguous)
+{
+    const NormF n = null_norm_f(H, g, y);
+    const float thr = eps * fabsf(n.den);
+    ambiguous = fabsf(fabsf(n.norm) - thr) <= 9.5367431640625e-7f * n.size;
+    return !(fabsf(n.norm) <= thr);
+}
+
+// ---- double-single arithmetic -------------------------------------------
+// A value carried as an unevaluated sum hi + lo of two floats (about 48
+// significant bits), with the error-free transformations of Knuth (TwoSum)
+// and Dekker (TwoProduct by fused multiply-add).  The tracer uses it only on
+// the rare path that re-takes an ambiguous Eq. 4 test, so that the test is
+// decided to ~2^-40 of its terms without leaving the single-precision pipe
+// (GB300's FP64 rate is 1/64 of FP32's).
+struct ds {
+    float hi, lo;
+};
+__device__ __forceinline__ ds ds_two_sum(float a, float b)
+{
+    const float s = a + b, bb = s - a;
+    return ds{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ds ds_fast(float a, float b) // |a| >= |b| or a == 0
+{
+    const float s = a + b;
+    return ds{s, b - (s - a)};
+}
+__device__ __forceinline__ ds ds_add(ds x, ds y)
+{
+    const ds s = ds_two_sum(x.hi, y.hi);
+    return ds_fast(s.hi, s.lo + (x.lo + y.lo));
+}
+__device__ __forceinline__ ds ds_neg(ds x) { return ds{-x.hi, -x.lo}; }
+__device__ __forceinline__ ds ds_mul(ds x, ds y)
+{
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return ds_fast(p, e);
+}
+__device__ __forceinline__ ds ds_mulf(ds x, float y)
+{
+    const float p = x.hi * y;
+    float e = fmaf(x.hi, y, -p);
+    e = fmaf(x.lo, y, e);
+    return ds_fast(p, e);
+}
+// 1/x: the single-precision reciprocal refined by one Newton-Raphson step
+// r + r (1 - x r) whose residual 1 - x r is formed exactly.
+__device__ __forceinline__ ds ds_recip(ds x)
+{
+    const float r = 1.0f / x.hi;
+    const ds xr = ds_mulf(x, r);
+    const float e = (1.0f - xr.hi) - xr.lo;
+    return ds_fast(r, r * e);
+}
+
+// sin and cos of a float angle x (|x| < 8) in double-single, from a table
+// of sin and cos at the multiples x0 = j/32 (each as two floats, made in
+// double by sincos_table_kernel) and angle addition: d = x - x0 is exact,
+// |d| <= 1/64, and sin d = d - d^3/6 + d^5/120, cos d = 1 - d^2/2 + d^4/24
+// (truncation below 2e-15) need double-single only for d and d^2.
+constexpr int SINCOS_TABLE_HALF = 256; // entries j/32 for j in [-256, 256)
+__device__ __forceinline__ void ds_sincos(float x, const float4 *table, ds &s, ds &c)
+{
+    int j = (int)rintf(x * 32.0f);
+    j = j < -SINCOS_TABLE_HALF ? -SINCOS_TABLE_HALF : (j > SINCOS_TABLE_HALF - 1 ? SINCOS_TABLE_HALF - 1 : j);
+    const float4 t = table[j + SINCOS_TABLE_HALF];
+    const ds S0{t.x, t.y}, C0{t.z, t.w};
+    const float d = x - (float)j * 0.03125f; // exact
+    const float p = d * d, pe = fmaf(d, d, -p); // d^2 = p + pe exactly
+    const ds sd = ds_fast(d, d * p * fmaf(p, 1.0f / 120.0f, -1.0f / 6.0f));
+    const ds cd = ds_add(ds{1.0f, 0.0f}, ds{-0.5f * p, fmaf(p * p, 1.0f / 24.0f, -0.5f * pe)});
+    s = ds_add(ds_mul(S0, cd), ds_mul(C0, sd));
+    c = ds_add(ds_mul(C0, cd), ds_neg(ds_mul(S0, sd)));
+}
+
+// The null norm g(k, k) in double-single arithmetic of a compensated
+// single-precision state (the true state is hi - lo: y1 the high words, c1
+// the low ones) with the spin and mass split into two floats each, aM =
+// (a_hi, a_lo, M_hi, M_lo) and the sin/cos table of ds_sincos: accurate to
+// ~2^-40 of its terms, where single precision resolves ~2^-21.  Also returns
+// 1/Sigma (high word).
+__device__ __forceinline__ ds null_norm_ds(const float *y1, const float *c1, float4 aM, const float4 *table,
+                                         float &iS_hi)
+{
+    const ds r = ds_fast(y1[1], -c1[1]);
+    const ds kt = ds_fast(y1[4], -c1[4]), kr = ds_fast(y1[5], -c1[5]);
+    const ds kh = ds_fast(y1[6], -c1[6]), kp = ds_fast(y1[7], -c1[7]);
+    const ds a = ds_fast(aM.x, aM.y), M = ds_fast(aM.z, aM.w);
+    ds s, c;
+    ds_sincos(y1[2], table, s, c);
+    // sin and cos of theta_hi - theta_lo to first order in the low word
+    const float tl = c1[2];
+    const ds sn = ds_add(s, ds{-c.hi * tl, 0.0f});
+    const ds cs = ds_add(c, ds{s.hi * tl, 0.0f});
+    const ds r2 = ds_mul(r, r), a2 = ds_mul(a, a), s2 = ds_mul(sn, sn);
+    const ds Sigma = ds_add(r2, ds_mul(a2, ds_mul(cs, cs)));
+    const ds Delta = ds_add(ds_add(r2, ds_neg(ds_mulf(ds_mul(M, r), 2.0f))), a2);
+    const ds w = ds_add(kt, ds_neg(ds_mul(ds_mul(a, s2), kp)));
+    const ds v = ds_add(ds_mul(ds_add(r2, a2), kp), ds_neg(ds_mul(a, kt)));
+    const ds E = ds_add(ds_mul(s2, ds_mul(v, v)), ds_neg(ds_mul(Delta, ds_mul(w, w))));
+    const ds iS = ds_recip(Sigma), iD = ds_recip(Delta);
+    const ds q = ds_add(ds_mul(ds_mul(kr, kr), iD), ds_mul(kh, kh));
+    iS_hi = iS.hi;
+    return ds_add(ds_mul(Sigma, q), ds_mul(E, iS));
+}
+
+// The Eq. 4 test re-taken in double-single arithmetic: |g(k, k)| of
+// null_norm_ds against eps |g_tt (k^t)^2|.  The threshold needs no such care:
+// single precision forms it to ~2^-23 of itself.
+__device__ __forceinline__ bool xi_fails_ds(const float *y1, const float *c1, float4 aM, const float4 *table,
+                                            float eps)
+{
+    float iS;
+    const ds norm = null_norm_ds(y1, c1, aM, table, iS);
+    const float r = y1[1] - c1[1], kt = y1[4] - c1[4];
+    const float gtt = fmaf(-2.0f * aM.z * r, iS, 1.0f);
+    return !(fabsf(norm.hi + norm.lo) <= eps * fabsf(gtt * (kt * kt)));
 }
 
 // dk^mu/dl = -Gamma^mu_ab k^a k^b, from the closed-form symbols grouped with

@@ -26,6 +26,7 @@ FP64, FP32, FP32_KAHAN, FP32_KAHAN_SEL64 = 0, 1, 2, 3
 STEP_BENCH, STEP_EQ2 = 0, 1
 RENDER_PIXELS64, RENDER_PIXELS32, RENDER_RECORD, RENDER_INVARIANTS = 0, 1, 3, 4
 EVAL_CHRISTOFFEL, EVAL_RHS, EVAL_INITIAL, EVAL_XI, EVAL_SINCOS, EVAL_RECIP = 0, 1, 2, 3, 4, 5
+EVAL_SINCOS_DS, EVAL_NORM = 6, 7
 LAUNCH_PERSISTENT, LAUNCH_ONE_PER_THREAD = 0, 1
 GRID_CARTESIAN, GRID_POLAR = 0, 1
 RECORD = 17
@@ -151,6 +152,8 @@ def lib():
     L.gray_clear.restype = C.c_int
     L.gray_count_active.argtypes = [vp, vp, sz, i64, C.POINTER(i64), i32, C.POINTER(i64), vp]
     L.gray_count_active.restype = C.c_int
+    L.gray_range_stats.argtypes = [vp, vp, sz, i64, vp, i32, vp, vp]
+    L.gray_range_stats.restype = C.c_int
     L.gray_render.argtypes = [vp, vp, sz, i64, i64, i64, i32, vp, sz, vp]
     L.gray_render.restype = C.c_int
     L.gray_shadow.argtypes = [vp, vp, sz, i64, i64, C.POINTER(_Image), i32, vp, sz, vp]
@@ -167,6 +170,8 @@ def lib():
     L.gray_timings.restype = C.c_int
     L.gray_strerror.argtypes = [C.c_int]
     L.gray_strerror.restype = C.c_char_p
+    L.gray_fma_peak.argtypes = [i32, i32, i32, i64, vp, sz, vp]
+    L.gray_fma_peak.restype = C.c_int
     L.gray_launch_count.argtypes = []
     L.gray_launch_count.restype = i64
     _lib = L
@@ -309,6 +314,15 @@ def gray_setup_plan(ctx, images, state, n_state, first_ray=0, probe_stride=6, pr
     return order[:total]
 
 
+def gray_fma_peak(precision, blocks, threads, iters, sink, stream=None):
+    """Launch the FMA-chain microbenchmark (asynchronous); returns the
+    floating-point operations of the launch.  ``sink``: CUDA tensor of at
+    least blocks x threads elements of the precision's type."""
+    _check(lib().gray_fma_peak(int(precision), int(blocks), int(threads), int(iters), _ptr(sink),
+                               sink.numel() * sink.element_size(), _stream(stream)), "gray_fma_peak")
+    return 2 * 8 * int(iters) * int(blocks) * int(threads)
+
+
 def gray_set_timing(ctx, on=True):
     return _check(lib().gray_set_timing(ctx, 1 if on else 0), "gray_set_timing")
 
@@ -336,6 +350,18 @@ def gray_count_active(ctx, state, n_state, ranges, stream=None):
     _check(lib().gray_count_active(ctx, _ptr(state), state.numel() * state.element_size(), int(n_state), arr, k, out,
                                    _stream(stream)), "gray_count_active")
     return [int(out[j]) for j in range(k)]
+
+
+def gray_range_stats(ctx, state, n_state, ranges_dev, out_dev, n_ranges=None, stream=None):
+    """Asynchronous (active rays, steps) per range: ranges_dev an int64 CUDA
+    tensor of (first_ray, count) pairs, out_dev an int64 CUDA tensor of at
+    least 2 x n_ranges entries."""
+    if n_ranges is None:
+        n_ranges = ranges_dev.numel() // 2
+    assert ranges_dev.is_cuda and out_dev.is_cuda and out_dev.numel() >= 2 * n_ranges
+    return _check(lib().gray_range_stats(ctx, _ptr(state), state.numel() * state.element_size(), int(n_state),
+                                         _ptr(ranges_dev), int(n_ranges), _ptr(out_dev), _stream(stream)),
+                  "gray_range_stats")
 
 
 _PER = {RENDER_PIXELS64: 32, RENDER_PIXELS32: 16, RENDER_RECORD: 17 * 8, RENDER_INVARIANTS: 4 * 8}
@@ -406,8 +432,10 @@ def gray_eval(what, precision, inp, stream=None):
     """inp: float64 CUDA tensor of n rows (4, 10, 6 or 10 doubles by ``what``).
     Returns a float64 CUDA tensor of n rows (64, 8, 8 or 1 doubles)."""
     import torch
-    width_in = {EVAL_CHRISTOFFEL: 4, EVAL_RHS: 10, EVAL_INITIAL: 6, EVAL_XI: 10, EVAL_SINCOS: 1, EVAL_RECIP: 1}[what]
-    width_out = {EVAL_CHRISTOFFEL: 64, EVAL_RHS: 8, EVAL_INITIAL: 8, EVAL_XI: 1, EVAL_SINCOS: 2, EVAL_RECIP: 2}[what]
+    width_in = {EVAL_CHRISTOFFEL: 4, EVAL_RHS: 10, EVAL_INITIAL: 6, EVAL_XI: 10, EVAL_SINCOS: 1, EVAL_RECIP: 1,
+                EVAL_SINCOS_DS: 1, EVAL_NORM: 10}[what]
+    width_out = {EVAL_CHRISTOFFEL: 64, EVAL_RHS: 8, EVAL_INITIAL: 8, EVAL_XI: 1, EVAL_SINCOS: 2, EVAL_RECIP: 2,
+                 EVAL_SINCOS_DS: 2, EVAL_NORM: 6}[what]
     inp = inp.contiguous()
     n = inp.numel() // width_in
     out = torch.empty((n, width_out), dtype=torch.float64, device=inp.device)

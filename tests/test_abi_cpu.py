@@ -123,3 +123,22 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         gray.lib()
     with pytest.raises(RuntimeError):
         gray.Tracer(gray.Options(), 16)
+
+
+def test_noalloc_rejects_a_state_beyond_32_bit_ray_indices(L):
+    """gray_setup_noalloc takes the same state bound as gray_setup (ray
+    indices are 32-bit in the work queues): 2^31 rays are refused before any
+    CUDA call, even with a buffer size that would hold them."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("host-side validation test: runs where no GPU is visible")
+    except ImportError:
+        pass
+    im = (gray._Image * 1)(gray._Image(0.5, 1.0, 1000.0, 1.0, 1, 1, -1.0, 1.0, -1.0, 1.0, 0, 0))
+    n = 1 << 31
+    big = gray.gray_state_bytes(n, gray.FP64)
+    assert big > 0
+    assert L.gray_setup_noalloc(gray.FP64, im, 1, C.c_void_p(4096), big, n, 0, None) == gray.EINVAL
+    # one ray fewer passes validation and only then needs the device (absent here)
+    assert L.gray_setup_noalloc(gray.FP64, im, 1, C.c_void_p(4096), big, n - 1, 0, None) == gray.ECUDA

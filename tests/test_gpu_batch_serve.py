@@ -81,26 +81,49 @@ def test_clear_and_count_active():
     assert gray.gray_count_active(tr.ctx, tr.state, 300, [(0, 100), (100, 100), (200, 100)]) == [0, 100, 0]
     tr.trace(step_budget=5)
     assert gray.gray_count_active(tr.ctx, tr.state, 300, [(100, 100)]) == [100]
+    # the asynchronous form: ranges and results in device memory, clipped to the buffer
+    ranges = torch.tensor([0, 100, 100, 100, 150, 400, -50, 120], dtype=torch.int64, device="cuda")
+    out = torch.full((8,), -1, dtype=torch.int64, device="cuda")
+    gray.gray_range_stats(tr.ctx, tr.state, 300, ranges, out)
+    got = out.cpu().numpy()
+    assert list(got[0::2]) == [0, 100, 50, 0]
+    assert got[3] == 5 * 100 and got[5] == 5 * 50 and got[1] == 0 and got[7] == 0
     rc, n_active, _ = tr.trace()
     assert rc == 0 and n_active == 0
     rec = tr.records()
     assert np.all(rec[:100, 0] == gray.EMPTY) and np.all(rec[200:, 0] == gray.EMPTY)
+    gray.gray_range_stats(tr.ctx, tr.state, 300, ranges, out)
+    got = out.cpu().numpy()
+    assert list(got[0::2]) == [0, 0, 0, 0] and got[3] == rec[100:200, 1].sum()
     tr.close()
 
 
-def test_serving_result_is_the_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("plan_min_rays", [None, 0])
+def test_serving_result_is_the_same_alone_and_in_the_mix(plan_min_rays):
     """Continuous batching: requests admitted into a pool too small for all
-    of them at once, traced in budget-limited rounds together, give exactly
-    the image each gives when traced alone."""
+    of them at once, traced in budget-limited rounds together (two rounds
+    enqueued ahead of the host; with plan_min_rays = 0 each request planned
+    longest-first into the pool's queue), give exactly the image each gives
+    when traced alone, and their step counts add up."""
     reqs = I.request_stream(1000.0, 12, sides=(16, 24, 32, 48))
-    srv = serve.Server(OPT, capacity=4000, round_budget=64)
+    srv = serve.Server(OPT, capacity=4000, round_budget=64, plan_min_rays=plan_min_rays, probe_stride=3,
+                       probe_budget=50)
     stats = srv.run(reqs, realtime=False)
     srv.close()
     assert len(stats.results) == 12 and stats.rounds > 3
     by_id = {r.rid: r for r in stats.results}
+    steps = 0
     for q in reqs:
+        tr = gray.Tracer(OPT, q.image.n)
+        tr.setup([q.image])
+        tr.trace()
+        alone_rec = tr.records()
+        tr.close()
         alone = serve.render_alone(q.image, OPT)
         mixed = by_id[q.rid].pixels
         assert np.array_equal(alone, mixed)
+        assert by_id[q.rid].steps == alone_rec[:, 1].sum()
+        steps += alone_rec[:, 1].sum()
     s = stats.summary()
+    assert s["photon_steps"] == steps
     assert s["p99_ms"] >= s["p50_ms"] > 0
