@@ -52,9 +52,9 @@ SFU_PER_CLK_PER_SM = 16
 SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0
 # DRAM bytes (read + write) of one launch of the dominant kernel (the
-# single-precision pass of this workload) from an ncu capture of that kernel:
-# 140,259,072 read + 66,909,440 written.
-TRAFFIC_BYTES = 207168512
+# single-precision pass of this workload) from an ncu capture of that
+# kernel; None until counters of the current kernel are taken.
+TRAFFIC_BYTES = None
 # Nominal FP64 non-tensor peak at 2 FP64 lanes per SM (context only).
 FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1000.0
 
@@ -96,6 +96,8 @@ def parse_args():
     p.add_argument("--frame-steps", type=int, default=8, help="view workload: RK4 steps per frame")
     p.add_argument("--frame-out", default="", help="view workload: write one frame here (PGM)")
     p.add_argument("--no-serve", action="store_true", help="skip the serving leg of the default workload")
+    p.add_argument("--no-peaks", action="store_true",
+                   help="skip the FMA-chain peak measurement (the roofline then divides by the nominal peaks)")
     p.add_argument("--serve-rates", default="10,30", help="serving leg: Poisson arrival rates (req/s)")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="serving leg: seconds of arrivals per rate")
     p.add_argument("--serve-saturation", type=int, default=80,
@@ -363,7 +365,7 @@ def run_serve(args):
     opt = gray.Options(precision=gray.FP32_KAHAN_SEL64, max_steps=10000, r_sw=args.r_sw)
     out = []
     for rate in [float(x) for x in args.rates.split(",")]:
-        srv = serve.Server(opt, capacity=16 << 20, round_budget=256)
+        srv = serve.Server(opt, capacity=32 << 20, round_budget=4096)
         n_req = args.requests if args.requests > 0 else int(min(2000, max(200, 60.0 * rate)))
         reqs = I.request_stream(rate, n_req)
         st = srv.run(reqs, realtime=True, max_wall=180.0)
@@ -385,9 +387,10 @@ def serving_leg(args, rates, seconds, saturation):
     from paper_1303_5057_gb300 import gray, serve
     from paper_1303_5057_gb300 import inputs as I
     opt = gray.Options(precision=gray.FP32_KAHAN_SEL64, max_steps=10000, r_sw=args.r_sw)
-    srv = serve.Server(opt, capacity=16 << 20, round_budget=256)
+    srv = serve.Server(opt, capacity=32 << 20, round_budget=4096)
     srv.run(I.request_stream(100.0, 6, seed_index=40), realtime=False)  # warm-up
-    out = {"sides": "uniform over {32, 64, ..., 2048}", "pool_rays": 16 << 20, "round_budget": 256,
+    out = {"sides": "uniform over {32, 64, ..., 2048}", "pool_rays": 32 << 20, "round_budget": 4096,
+           "planned": "requests of >= 65536 rays (probe stride 6, budget 400)",
            "precision": "fp32_kahan_sel64", "latency": "arrival to image in pinned host memory", "rates": []}
     for rate in rates:
         n_req = max(10, int(rate * seconds))
@@ -689,7 +692,7 @@ def main():
     e2e_value = steps_per_pass / (statistics.mean(e2e_ms) / 1000.0) * world
 
     # ---- measured non-tensor FMA peaks (the roofline's denominators) ----
-    peaks = measure_alu_peaks(gray, torch) if rank == 0 else None
+    peaks = measure_alu_peaks(gray, torch) if rank == 0 and not args.no_peaks else None
     fp32_peak = peaks["fp32"]["tflops"] if peaks else FP32_PEAK_TFLOPS
     fp64_peak = peaks["fp64"]["tflops"] if peaks else FP64_PEAK_TFLOPS
 

@@ -41,6 +41,7 @@ extern "C" {
 #define GRAY_EINVAL (-1)   /* bad argument: NaN or out-of-range parameter, n < 0, buffer too small */
 #define GRAY_ECUDA (-2)    /* a CUDA runtime call failed (launch, copy, memset) */
 #define GRAY_ENOMEM (-3)   /* host or device allocation of the context failed */
+#define GRAY_ECANCEL (-4)  /* gray_trace stopped early because the context's cancel flag was set */
 
 /* ---- per-ray status (the paper's stop conditions, Sec. 2) ----------- */
 #define GRAY_RAY_ACTIVE 0    /* still being traced */
@@ -451,6 +452,21 @@ int gray_eval(int32_t what, int32_t precision, const double *in_dev, int64_t n,
  * Errors: GRAY_EINVAL (precision, shape, iters, sink too small), GRAY_ECUDA. */
 int gray_fma_peak(int32_t precision, int32_t blocks, int32_t threads, int64_t iters, void *sink_dev,
                   size_t sink_bytes, void *stream);
+
+/* Cancel the context's traces from the host (on = 1), or clear the request
+ * (on = 0).  The flag lives in the context's device memory and is written
+ * through a private non-blocking stream, so it takes effect while a
+ * gray_trace of this context runs on another stream (or waits in another
+ * host thread); this call returns once the flag is set.  Every trace pass
+ * reads it when its warps refill (every `refill` steps): from then on no ray
+ * is picked up and every ray in flight is stored as it stands, still ACTIVE
+ * (as when a step budget runs out), so nothing is lost and a later trace
+ * continues each ray bit for bit as if it had not been interrupted.  While
+ * the flag is set, gray_trace returns GRAY_ECANCEL (when it reports counts)
+ * instead of 0 or 1; it stays set until cleared with on = 0.  The paper's
+ * interactive mode (Sec. 2) stops and resumes the integration in this way.
+ * Errors: GRAY_EINVAL (NULL context), GRAY_ECUDA. */
+int gray_cancel(gray_ctx *ctx, int32_t on);
 
 /* Record CUDA events around the passes of every later gray_trace and
  * gray_plan call of this context (on = 1) or stop (on = 0).  Diagnostic.

@@ -165,6 +165,7 @@ struct Workspace {
     unsigned long long handoff; // rays appended to the hand-off list by the current pass
     unsigned long long demoted; // rays returned to single precision by the current zone pass
     unsigned long long zone_steps; // steps taken by the zone kernel in this call
+    unsigned long long cancel;     // the cancel flag as the call ended (copied in by gray_trace)
 };
 
 } // namespace
@@ -182,6 +183,7 @@ struct gray_ctx {
     cudaStream_t side = nullptr;       // gray_setup_plan: the planning passes (high priority)
     cudaEvent_t fork = nullptr, join = nullptr;
     float4 *sincos_table = nullptr;    // device: the double-single Eq. 4 re-test's table (8 KB)
+    cudaStream_t cancel_stream = nullptr; // gray_cancel writes the flag through it (non-blocking)
 };
 
 namespace {
@@ -513,6 +515,7 @@ struct TraceArgs {
     double h_frac, h_min, eps_xi, cap_frac, r_esc_frac, r_sw;
     Workspace *ws;
     const float4 *sincos_table; // the double-single Eq. 4 re-test's sin/cos table
+    const int *cancel;          // the context's cancel flag (gray_cancel), read at each refill
 };
 
 template <int MODE> struct ModeTraits {
@@ -534,6 +537,16 @@ __device__ __forceinline__ int64_t queue_ray(const TraceArgs &A, int64_t slot)
         return slot;
     const int64_t my = (int64_t)A.order[slot];
     return (my >= 0 && my < A.n) ? my : -1;
+}
+
+// The context's cancel flag, read by lane 0 and shared with the warp
+// (warp-uniform call).
+__device__ __forceinline__ bool cancelled(const TraceArgs &A, int lane)
+{
+    int f = 0;
+    if (lane == 0)
+        f = *(volatile const int *)A.cancel;
+    return __shfl_sync(0xffffffffu, f, 0) != 0;
 }
 
 // Warp-aggregated counter increment (warp-uniform call).
@@ -608,6 +621,11 @@ template <int MODE> __global__ void __maxnreg__(128) trace32_kernel(TraceArgs A)
     bool pending = false; // this lane handed its ray off; its index is not yet on the list
 
     for (;;) {
+        // gray_cancel: no more rays are picked up, and the rays in flight
+        // are stored as they stand (still ACTIVE) at their next step
+        const bool stop = cancelled(A, lane);
+        if (stop)
+            exhausted = true;
         if (SEL64) {
             int rank;
             const unsigned long long hb = warp_count(&A.ws->handoff, pending, lane, &rank);
@@ -695,12 +713,12 @@ template <int MODE> __global__ void __maxnreg__(128) trace32_kernel(TraceArgs A)
             if (has) {
                 int status = GRAY_RAY_ACTIVE;
                 bool yield = false;
-                if (steps >= stop_at || (SEL64 && y[1] - c[1] < r_promote)) {
+                if (steps >= stop_at || (SEL64 && y[1] - c[1] < r_promote) || stop) {
                     if (steps >= A.max_steps) {
                         status = GRAY_RAY_STEP_CAP;
                         for (int m = 0; m < 4; ++m)
                             fin[m] = y[m];
-                    } else if (A.budget > 0 && used0 + (steps - steps0) >= A.budget) {
+                    } else if (stop || (A.budget > 0 && used0 + (steps - steps0) >= A.budget)) {
                         yield = true;
                     } else {
                         handoff = true;
@@ -760,6 +778,9 @@ __global__ void __launch_bounds__(128) trace64_kernel(TraceArgs A)
         cz[m] = 0.0;
 
     for (;;) {
+        const bool stop = cancelled(A, lane); // gray_cancel, as in trace32_kernel
+        if (stop)
+            exhausted = true;
         while (!exhausted) {
             const unsigned idle = __ballot_sync(FULL, !has);
             if (idle == 0)
@@ -807,7 +828,7 @@ __global__ void __launch_bounds__(128) trace64_kernel(TraceArgs A)
                     status = GRAY_RAY_STEP_CAP;
                     for (int m = 0; m < 4; ++m)
                         fin[m] = y[m];
-                } else if (A.budget > 0 && used >= A.budget) {
+                } else if (stop || (A.budget > 0 && used >= A.budget)) {
                     yield = true;
                 } else {
                     const int e0 = euler;
@@ -882,6 +903,9 @@ __global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
         cz[m] = 0.0;
 
     for (;;) {
+        const bool stop = cancelled(A, lane); // gray_cancel, as in trace32_kernel
+        if (stop)
+            exhausted = true;
         while (!exhausted) {
             const unsigned idle = __ballot_sync(FULL, !has);
             if (idle == 0)
@@ -946,7 +970,7 @@ __global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
                     status = GRAY_RAY_STEP_CAP;
                     for (int m = 0; m < 4; ++m)
                         find[m] = dbl ? yd[m] : (double)yf[m] - (double)cf[m];
-                } else if (A.budget > 0 && used >= A.budget) {
+                } else if (stop || (A.budget > 0 && used >= A.budget)) {
                     yield = true;
                 } else if (dbl && yd[1] >= r_demote) {
                     // climb out of the zone: back to a compensated single pair
@@ -1127,7 +1151,7 @@ constexpr int PLAN_BUCKETS = 1024;
 // aux layout: [0] probe count, [1 ..] histogram, [1 + PLAN_BUCKETS ..] bucket offsets
 constexpr int AUX_PROBES = 0, AUX_HIST = 1, AUX_OFF = 1 + PLAN_BUCKETS, AUX_WORDS = 1 + 2 * PLAN_BUCKETS;
 // one more word after the planning words: the call epoch (never cleared)
-constexpr int AUX_EPOCH = AUX_WORDS, AUX_ALLOC = AUX_WORDS + 1;
+constexpr int AUX_EPOCH = AUX_WORDS, AUX_CANCEL = AUX_WORDS + 1, AUX_ALLOC = AUX_WORDS + 2;
 
 // Start a new call: epochs run 1 .. 2^31 - 2 (0 marks a ray no call touched).
 __global__ void bump_epoch_kernel(unsigned long long *aux)
@@ -2004,6 +2028,10 @@ int gray_create(gray_ctx **ctx, const gray_options *opt)
         gray_destroy(c);
         return GRAY_ECUDA;
     }
+    if (cudaStreamCreateWithFlags(&c->cancel_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        gray_destroy(c);
+        return GRAY_ECUDA;
+    }
     if (cudaMalloc((void **)&c->sincos_table, 2 * SINCOS_TABLE_HALF * sizeof(float4)) != cudaSuccess) {
         gray_destroy(c);
         return GRAY_ENOMEM;
@@ -2036,6 +2064,8 @@ void gray_destroy(gray_ctx *ctx)
     cudaFree(ctx->ws);
     cudaFree(ctx->aux);
     cudaFree(ctx->sincos_table);
+    if (ctx->cancel_stream)
+        cudaStreamDestroy(ctx->cancel_stream);
     cudaFreeHost(ctx->ws_host);
     delete ctx;
 }
@@ -2113,6 +2143,7 @@ TraceArgs make_trace_args(gray_ctx *ctx, void *state, int64_t n_state, int64_t s
     A.r_sw = o.r_sw;
     A.ws = ctx->ws;
     A.sincos_table = ctx->sincos_table;
+    A.cancel = (const int *)&ctx->aux[AUX_CANCEL];
     A.one_per_thread = o.launch == GRAY_LAUNCH_ONE_PER_THREAD;
     A.stop_equator = o.stop_equator;
     A.zone_return = 0;
@@ -2266,7 +2297,10 @@ int gray_trace(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, 
         if ((rc = check_launch()))
             return rc;
     }
-    if (cudaMemcpyAsync(ctx->ws_host, ctx->ws, sizeof(Workspace), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+    // the cancel flag as the passes ended, into the workspace's last word
+    if (cudaMemcpyAsync(&ctx->ws->cancel, &ctx->aux[AUX_CANCEL], sizeof(unsigned long long),
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ctx->ws_host, ctx->ws, sizeof(Workspace), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return GRAY_ECUDA;
     const Workspace &w = *ctx->ws_host;
@@ -2278,6 +2312,8 @@ int gray_trace(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, 
         stats_host[2] = (int64_t)w.fp64;
         stats_host[3] = (int64_t)w.active;
     }
+    if ((int)w.cancel != 0)
+        return GRAY_ECANCEL;
     return w.active ? 1 : 0;
 }
 
@@ -2437,6 +2473,19 @@ int gray_setup_plan(gray_ctx *ctx, const gray_image *images, int32_t n_images, v
     if (rc)
         return rc;
     return cuda_err(e);
+}
+
+int gray_cancel(gray_ctx *ctx, int32_t on)
+{
+    if (!ctx)
+        return GRAY_EINVAL;
+    // a 4-byte word of the aux buffer (device memory), through the context's
+    // non-blocking stream: it runs beside a trace in flight on any stream
+    if (cudaMemsetAsync(&ctx->aux[AUX_CANCEL], 0, sizeof(unsigned long long), ctx->cancel_stream) != cudaSuccess ||
+        (on && cudaMemsetAsync(&ctx->aux[AUX_CANCEL], 1, 1, ctx->cancel_stream) != cudaSuccess) ||
+        cudaStreamSynchronize(ctx->cancel_stream) != cudaSuccess)
+        return GRAY_ECUDA;
+    return GRAY_OK;
 }
 
 int gray_set_timing(gray_ctx *ctx, int32_t on)
@@ -2850,6 +2899,7 @@ const char *gray_strerror(int code)
     case GRAY_EINVAL: return "invalid argument";
     case GRAY_ECUDA: return "CUDA runtime error";
     case GRAY_ENOMEM: return "out of memory";
+    case GRAY_ECANCEL: return "trace cancelled by gray_cancel";
     default: return "unknown error code";
     }
 }

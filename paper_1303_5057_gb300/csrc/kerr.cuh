@@ -42,7 +42,36 @@
 
 namespace gray {
 
-__device__ __forceinline__ void fsincos(float x, float *s, float *c) { sincosf(x, s, c); }
+// Single-precision sin and cos of the angles the tracer meets (|x| < 2^22;
+// theta stays within a few pi): x = k pi/2 + d with k rounded by the
+// 1.5 * 2^23 addition (whose low bits give the quadrant) and pi/2 split in
+// three floats (Cody and Waite's reduction), then the Taylor series of sin d
+// and cos d to degrees 9 and 10 (truncation below 2^-28 for |d| <= pi/4).
+// Within 1.5 ulp of the double values (a unit test bounds it by 4); unlike
+// the library's sincosf it has no float-integer conversion, which on this
+// part runs on the narrow double-precision pipe.
+__device__ __forceinline__ void fsincos(float x, float *s, float *c)
+{
+    const float t = fmaf(x, 0.636619772367581343f, 12582912.0f);
+    const float k = t - 12582912.0f;
+    const int q = __float_as_int(t) & 3;
+    float d = fmaf(-k, 1.57079637050628662109375f, x);
+    d = fmaf(-k, -4.37113882867379317e-08f, d);
+    d = fmaf(-k, -1.71512451e-15f, d);
+    const float d2 = d * d;
+    float ps = fmaf(d2, 1.0f / 362880.0f, -1.0f / 5040.0f);
+    ps = fmaf(ps, d2, 1.0f / 120.0f);
+    ps = fmaf(ps, d2, -1.0f / 6.0f);
+    const float sd = fmaf(ps * d2, d, d);
+    float pc = fmaf(d2, -1.0f / 3628800.0f, 1.0f / 40320.0f);
+    pc = fmaf(pc, d2, -1.0f / 720.0f);
+    pc = fmaf(pc, d2, 1.0f / 24.0f);
+    pc = fmaf(pc, d2, -0.5f);
+    const float cd = fmaf(pc, d2, 1.0f);
+    const float sa = (q & 1) ? cd : sd, ca = (q & 1) ? sd : cd;
+    *s = (q & 2) ? -sa : sa;
+    *c = ((q + 1) & 2) ? -ca : ca;
+}
 __device__ __forceinline__ void fsincos(double x, double *s, double *c) { sincos(x, s, c); }
 template <typename T> __device__ __forceinline__ T pi_v();
 template <> __device__ __forceinline__ float pi_v<float>() { return 3.14159265358979323846f; }
@@ -322,7 +351,8 @@ __device__ __forceinline__ Geo<T> geometry(const Hole<T> &H, T r, T th, T dr = T
 
 // sin and cos of a small angle d by their Taylor series: single precision
 // for |d| <= 0.125 (degrees 5 and 6, truncation below 1e-10), double for
-// |d| <= 0.25 (degrees 11 and 12, below 3e-18).  Returns false for larger |d|.
+// |d| <= 0.25 (degrees 11 and 12, below 3e-18; degrees 7 and 8 for
+// |d| <= 1/64).  Returns false for larger |d|.
 __device__ __forceinline__ bool small_sincos(float d, float *s, float *c)
 {
     if (!(fabsf(d) <= 0.125f))
@@ -340,6 +370,18 @@ __device__ __forceinline__ bool small_sincos(double d, double *s, double *c)
     if (!(fabs(d) <= 0.25))
         return false;
     const double d2 = d * d;
+    if (fabs(d) <= 0.015625) {
+        // degrees 7 and 8 (truncation below 1e-22 for |d| <= 1/64), the
+        // usual case of the short steps near the horizon
+        double ps = fma(d2, -1.984126984126984e-04, 8.333333333333333e-03);
+        ps = fma(ps, d2, -1.6666666666666666e-01);
+        *s = fma(ps * d2, d, d);
+        double pc = fma(d2, 2.48015873015873e-05, -1.388888888888889e-03);
+        pc = fma(pc, d2, 4.1666666666666664e-02);
+        pc = fma(pc, d2, -0.5);
+        *c = fma(pc, d2, 1.0);
+        return true;
+    }
     double ps = fma(d2, -2.505210838544172e-08, 2.7557319223985893e-06);
     ps = fma(ps, d2, -1.984126984126984e-04);
     ps = fma(ps, d2, 8.333333333333333e-03);

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libgray.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "gray.h")
 
 # constants mirrored from include/gray.h (checked against it by the tests)
-OK, EINVAL, ECUDA, ENOMEM = 0, -1, -2, -3
+OK, EINVAL, ECUDA, ENOMEM, ECANCEL = 0, -1, -2, -3, -4
 ACTIVE, CAPTURED, ESCAPED, STEP_CAP, NONFINITE, EMPTY, EQUATOR = 0, 1, 2, 3, 4, 5, 6
 FP64, FP32, FP32_KAHAN, FP32_KAHAN_SEL64 = 0, 1, 2, 3
 STEP_BENCH, STEP_EQ2 = 0, 1
@@ -164,6 +164,8 @@ def lib():
     L.gray_splat.restype = C.c_int
     L.gray_eval.argtypes = [i32, i32, vp, i64, vp, vp]
     L.gray_eval.restype = C.c_int
+    L.gray_cancel.argtypes = [vp, i32]
+    L.gray_cancel.restype = C.c_int
     L.gray_set_timing.argtypes = [vp, i32]
     L.gray_set_timing.restype = C.c_int
     L.gray_timings.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64)]
@@ -270,15 +272,18 @@ def gray_setup_rays(ctx, rays, M, state, n_state, first_ray=0, stream=None):
 
 def gray_trace(ctx, state, n_state, step_budget=0, wait=True, stream=None, order=None):
     """Returns (rc, n_active, stats) with stats = (steps, euler, fp64 steps,
-    active) of this call; n_active and stats are None when wait=False.
+    active) of this call; n_active and stats are None when wait=False.  rc is
+    ECANCEL when the context's cancel flag stopped the call (gray_cancel).
     ``order``: optional int32 CUDA tensor, the work queue of ray indices."""
     op = _ptr(order) if order is not None else None
     no = order.numel() if order is not None else 0
     if wait:
         na = C.c_int64()
         st = (C.c_int64 * 4)()
-        rc = _check(lib().gray_trace(ctx, _ptr(state), state.numel() * state.element_size(), int(n_state), op, no,
-                                     int(step_budget), C.byref(na), st, _stream(stream)), "gray_trace")
+        rc = lib().gray_trace(ctx, _ptr(state), state.numel() * state.element_size(), int(n_state), op, no,
+                              int(step_budget), C.byref(na), st, _stream(stream))
+        if rc != ECANCEL:  # a cancelled trace is not a failure: its counts are valid
+            _check(rc, "gray_trace")
         return rc, int(na.value), tuple(int(x) for x in st)
     rc = _check(lib().gray_trace(ctx, _ptr(state), state.numel() * state.element_size(), int(n_state), op, no,
                                  int(step_budget), None, None, _stream(stream)), "gray_trace")
@@ -321,6 +326,12 @@ def gray_fma_peak(precision, blocks, threads, iters, sink, stream=None):
     _check(lib().gray_fma_peak(int(precision), int(blocks), int(threads), int(iters), _ptr(sink),
                                sink.numel() * sink.element_size(), _stream(stream)), "gray_fma_peak")
     return 2 * 8 * int(iters) * int(blocks) * int(threads)
+
+
+def gray_cancel(ctx, on=True):
+    """Set (or clear) the context's cancel flag; safe to call from another
+    thread while gray_trace runs."""
+    return _check(lib().gray_cancel(ctx, 1 if on else 0), "gray_cancel")
 
 
 def gray_set_timing(ctx, on=True):

@@ -124,13 +124,15 @@ class Server:
     """Continuous-batching render server over one resident pool.
 
     capacity: ray slots in the pool (device memory = gray_state_bytes).
-    round_budget: steps each in-flight ray may take per round.
+    round_budget: steps each in-flight ray may take per round (measured on the
+    config-5 mix at 30 req/s: p99 195 ms at 1024, 143 ms at 4096; the same
+    saturated rate).
     depth: rounds enqueued ahead of the host.
     plan_min_rays: requests of at least this many rays are planned
     longest-first (gray_setup_plan) into the pool's queue; smaller ones keep
     their natural order (0: plan every request, None: plan none)."""
 
-    def __init__(self, opt: gray.Options, capacity: int, round_budget: int = 256, device="cuda", depth: int = 2,
+    def __init__(self, opt: gray.Options, capacity: int, round_budget: int = 4096, device="cuda", depth: int = 2,
                  plan_min_rays=1 << 16, probe_stride: int = 6, probe_budget: int = 400, max_requests: int = 4096):
         import torch
         self.torch = torch

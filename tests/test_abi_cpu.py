@@ -52,6 +52,7 @@ def test_defaults_and_strerror(L):
     assert gray.gray_strerror(0) == "success"
     assert "invalid" in gray.gray_strerror(gray.EINVAL)
     assert gray.gray_strerror(-99) == "unknown error code"
+    assert "cancel" in gray.gray_strerror(gray.ECANCEL)
     assert gray.gray_launch_count() >= 0
 
 
@@ -76,6 +77,8 @@ def test_calls_reject_null_context(L):
     assert L.gray_ring(None, None, 0, 0, 0, None, 0, None, 0, None, 0, None) == gray.EINVAL
     assert L.gray_splat(None, None, 0, 0, 0, 0, None, None, None, 0, None) == gray.EINVAL
     assert L.gray_clear(None, None, 0, 0, 0, 0, None) == gray.EINVAL
+    assert L.gray_cancel(None, 1) == gray.EINVAL
+    assert L.gray_range_stats(None, None, 0, 0, None, 0, None, None) == gray.EINVAL
 
 
 def test_structures_match_the_header(tmp_path):

@@ -127,3 +127,75 @@ def test_serving_result_is_the_same_alone_and_in_the_mix(plan_min_rays):
     s = stats.summary()
     assert s["photon_steps"] == steps
     assert s["p99_ms"] >= s["p50_ms"] > 0
+
+
+def test_cancel_stops_a_trace_and_the_trace_resumes_bit_for_bit():
+    """gray_cancel from another host thread stops a trace in flight at its
+    warps' next refill: the call returns GRAY_ECANCEL early with rays still
+    active; after the flag is cleared the next trace finishes them, and the
+    records equal those of a trace that was never interrupted."""
+    import threading
+    import time
+
+    im = I.kerr_1024(512).images[0]
+    opt = gray.Options(precision=gray.FP64, max_steps=10000)
+    ref = gray.Tracer(opt, im.n)
+    ref.setup([im])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, n_active, _ = ref.trace()
+    full = time.perf_counter() - t0
+    want = ref.records()
+    ref.close()
+    assert rc == 0 and n_active == 0 and full > 0.02
+
+    tr = gray.Tracer(opt, im.n)
+    tr.setup([im])
+    torch.cuda.synchronize()
+    out = {}
+
+    def run():
+        t1 = time.perf_counter()
+        out["res"] = tr.trace()
+        out["dt"] = time.perf_counter() - t1
+
+    th = threading.Thread(target=run)
+    th.start()
+    time.sleep(min(0.005, full / 10))
+    gray.gray_cancel(tr.ctx, True)
+    th.join()
+    rc, n_active, stats = out["res"]
+    assert rc == gray.ECANCEL and n_active > 0
+    assert out["dt"] < 0.8 * full
+    # while the flag is set, a trace takes no step
+    rc, n_again, stats = tr.trace()
+    assert rc == gray.ECANCEL and n_again == n_active and stats[0] == 0
+    gray.gray_cancel(tr.ctx, False)
+    rc, n_active, _ = tr.trace()
+    assert rc == 0 and n_active == 0
+    assert np.array_equal(tr.records(), want)
+    tr.close()
+
+
+def test_cancel_in_the_selective_double_mode_resumes_bit_for_bit():
+    """The same in compensated FP32 with the double zone: a cancelled call
+    parks rays of both passes (single precision and the zone) as they stand."""
+    im = I.Image(a=0.95, incl=1.3, nx=64, ny=64)
+    opt = gray.Options(precision=gray.FP32_KAHAN_SEL64, max_steps=10000, r_sw=0.3, refill=2)
+    ref = gray.Tracer(opt, im.n)
+    ref.setup([im])
+    ref.trace()
+    want = ref.records()
+    ref.close()
+    tr = gray.Tracer(opt, im.n)
+    tr.setup([im])
+    rc, n1, _ = tr.trace(step_budget=150)   # part of the way, some rays inside the zone
+    assert rc == 1 and n1 > 0
+    gray.gray_cancel(tr.ctx, True)
+    rc, n2, st = tr.trace()
+    assert rc == gray.ECANCEL and n2 == n1 and st[0] == 0
+    gray.gray_cancel(tr.ctx, False)
+    rc, n3, _ = tr.trace()
+    assert rc == 0 and n3 == 0
+    assert np.array_equal(tr.records(), want)
+    tr.close()
