@@ -56,7 +56,12 @@ extern "C" {
 #define GRAY_FP64 0             /* every step in double precision */
 #define GRAY_FP32 1             /* every step in single precision */
 #define GRAY_FP32_KAHAN 2       /* single precision, compensated (Kahan) state update */
-#define GRAY_FP32_KAHAN_SEL64 3 /* as GRAY_FP32_KAHAN, with steps near the horizon promoted to double */
+#define GRAY_FP32_KAHAN_SEL64 3 /* as GRAY_FP32_KAHAN, with steps near the horizon promoted to extended
+                                   precision (zone_arith: double-single or double) */
+
+/* ---- arithmetic of the near-horizon zone of GRAY_FP32_KAHAN_SEL64 ---- */
+#define GRAY_ZONE_DS 0   /* double-single (two floats, ~48-bit significand) on the FP32 pipe */
+#define GRAY_ZONE_FP64 1 /* IEEE double on the FP64 pipe (1/64 of the FP32 rate on this part) */
 
 /* ---- step-size rule ------------------------------------------------- */
 #define GRAY_STEP_BENCH 0 /* |h| = max(min(h_frac r, (r - r_h)/(2|k^r|)), h_min) */
@@ -128,12 +133,15 @@ typedef struct gray_options {
     int32_t refill;        /* steps between warp refills from the work queue, 0 = default */
     int32_t launch;        /* GRAY_LAUNCH_PERSISTENT or GRAY_LAUNCH_ONE_PER_THREAD (single precision only) */
     int32_t stop_equator;  /* 1: also stop at the first crossing of theta = pi/2 (the grid projection of Sec. 3) */
+    int32_t zone_arith;    /* GRAY_FP32_KAHAN_SEL64: GRAY_ZONE_DS (default) or GRAY_ZONE_FP64 */
+    int32_t reserved;      /* must be 0 */
     double h_frac;         /* 1/32: the f of the benchmark rule, the Delta of Eq. 2 */
     double h_min;          /* 1e-3: floor on |h| */
     double cap_frac;       /* 1.01: capture when r <= cap_frac * r_h */
     double eps_xi;         /* 1e-3: Euler redo when |xi + 1| > eps_xi (Eq. 4) */
     double r_esc_frac;     /* 1.0: escape radius = r_esc_frac * r_obs */
-    double r_sw;           /* GRAY_FP32_KAHAN_SEL64: steps with r < cap_frac r_h + r_sw run in double */
+    double r_sw;           /* GRAY_FP32_KAHAN_SEL64: steps with r < cap_frac r_h + r_sw run in the zone's
+                              extended precision (zone_arith) */
 } gray_options;
 
 /* Per-ray output of GRAY_RENDER_PIXELS64: final position on the stop

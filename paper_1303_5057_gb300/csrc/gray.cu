@@ -25,6 +25,7 @@
 
 #include <atomic>
 #include <cmath>
+#include <type_traits>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -182,7 +183,6 @@ struct gray_ctx {
     bool ev_used[3] = {false, false, false};
     cudaStream_t side = nullptr;       // gray_setup_plan: the planning passes (high priority)
     cudaEvent_t fork = nullptr, join = nullptr;
-    float4 *sincos_table = nullptr;    // device: the double-single Eq. 4 re-test's table (8 KB)
     cudaStream_t cancel_stream = nullptr; // gray_cancel writes the flag through it (non-blocking)
 };
 
@@ -330,22 +330,22 @@ __device__ __forceinline__ void add_update(const T *y, const T *c, const T *inc,
 }
 
 // Eq. 3 on the state; with compensation the new theta and phi are formed in
-// double from hi - lo so that the remap itself adds no rounding.
+// double-single from the pair (hi, lo) so that the remap itself adds no
+// rounding beyond the pair's own.
 template <typename T, bool KAHAN> __device__ __forceinline__ int remap_eq3(T *y, T *c)
 {
     const T pi = pi_v<T>();
     if (!(y[2] > pi) && !(y[2] < T(0)))
         return 0;
     const bool over = y[2] > pi;
-    if (KAHAN) {
-        const double th = (double)y[2] - (double)c[2];
-        const double ph = (double)y[3] - (double)c[3];
-        const double th2 = over ? 2.0 * 3.14159265358979323846 - th : -th;
-        const double ph2 = over ? ph + 3.14159265358979323846 : ph - 3.14159265358979323846;
-        y[2] = (T)th2;
-        c[2] = (T)((double)y[2] - th2);
-        y[3] = (T)ph2;
-        c[3] = (T)((double)y[3] - ph2);
+    if constexpr (KAHAN) {
+        const ds th = ds_fast(y[2], -c[2]), ph = ds_fast(y[3], -c[3]);
+        const ds th2 = over ? ds(2.0 * 3.14159265358979323846) - th : -th;
+        const ds ph2 = over ? ph + pi_v<ds>() : ph - pi_v<ds>();
+        y[2] = th2.hi;
+        c[2] = -th2.lo;
+        y[3] = ph2.hi;
+        c[3] = -ph2.lo;
         y[6] = -y[6];
         c[6] = -c[6];
     } else {
@@ -365,6 +365,8 @@ __device__ __forceinline__ float sixth(float h) { return h * (1.0f / 6.0f); }
 __device__ __forceinline__ double sixth(double h) { return h * (1.0 / 6.0); }
 __device__ __forceinline__ float ninth(float h) { return h * (1.0f / 9.0f); }
 __device__ __forceinline__ double ninth(double h) { return h * (1.0 / 9.0); }
+__device__ __forceinline__ ds sixth(ds h) { return h * ds(1.0 / 6.0); }
+__device__ __forceinline__ ds ninth(ds h) { return h * ds(1.0 / 9.0); }
 
 // One step.  Returns the ray's new status; writes fin[4] when it stops.  g
 // holds the geometry of the current point on entry and of the new point on
@@ -373,8 +375,7 @@ __device__ __forceinline__ double ninth(double h) { return h * (1.0 / 9.0); }
 // the stop surfaces are interpolated by stop_surface_mixed.
 template <typename T, bool KAHAN, bool MIXED_STOP = false>
 __device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, T *y, T *c, Geo<T> &g, T *fin,
-                                         int &euler, int &remaps, const float2 *aM_lo = nullptr,
-                                         const float4 *sincos_table = nullptr)
+                                         int &euler, int &remaps, const float2 *aM_lo = nullptr)
 {
     T h = step_size(H, O, y);
     T a1[4], a2[4], a3[4], a4[4];
@@ -415,9 +416,9 @@ __device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, 
     if constexpr (sizeof(T) == 4 && KAHAN) {
         bool ambiguous;
         redo = xi_fails_flag(H, g1, y1, O.eps_xi, ambiguous);
-        if (ambiguous && aM_lo && sincos_table) {
+        if (ambiguous && aM_lo) {
             const float2 lo = *aM_lo;
-            redo = xi_fails_ds(y1, c1, make_float4(H.a, lo.x, H.M, lo.y), sincos_table, O.eps_xi);
+            redo = xi_fails_ds(y1, c1, make_float4(H.a, lo.x, H.M, lo.y), O.eps_xi);
         }
     } else {
         redo = xi_fails(H, g1, y1, O.eps_xi);
@@ -438,7 +439,7 @@ __device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, 
     bool finite = true;
 #pragma unroll
     for (int m = 0; m < 8; ++m)
-        finite &= isfinite(y1[m]);
+        finite &= finite_v(y1[m]);
     // The rare outcomes (a non-finite state, a stop, a pole crossing) sit
     // behind one test, so a plain step takes a single branch here.
     const T half_pi = T(0.5) * pi_v<T>();
@@ -514,7 +515,6 @@ struct TraceArgs {
     int zone_return;    // zone pass: a ray climbing out of the zone goes to the return list
     double h_frac, h_min, eps_xi, cap_frac, r_esc_frac, r_sw;
     Workspace *ws;
-    const float4 *sincos_table; // the double-single Eq. 4 re-test's sin/cos table
     const int *cancel;          // the context's cancel flag (gray_cancel), read at each refill
 };
 
@@ -724,8 +724,7 @@ template <int MODE> __global__ void __maxnreg__(128) trace32_kernel(TraceArgs A)
                         handoff = true;
                     }
                 } else {
-                    status = step_once<float, KAHAN>(H, O, y, c, geo, fin, euler, remaps, (const float2 *)&v.P[id].w,
-                                                     A.sincos_table);
+                    status = step_once<float, KAHAN>(H, O, y, c, geo, fin, euler, remaps, (const float2 *)&v.P[id].w);
                     ++steps;
                 }
                 if (status != GRAY_RAY_ACTIVE || yield || handoff) {
@@ -853,27 +852,52 @@ __global__ void __launch_bounds__(128) trace64_kernel(TraceArgs A)
     warp_stats<double>(A, lane, tot_steps, tot_euler, 0ull);
 }
 
+// The zone's arithmetic T: double, or double-single (ds) on the FP32 pipe.
+// Conversions from and to a compensated single-precision pair (the true value
+// is hi - c) and to a float.
+template <typename T> struct ZoneArith;
+template <> struct ZoneArith<double> {
+    static __device__ __forceinline__ double from_pair(float hi, float c) { return (double)hi - (double)c; }
+    static __device__ __forceinline__ void to_pair(double v, float &hi, float &c)
+    {
+        hi = (float)v;
+        c = (float)((double)hi - v);
+    }
+    static __device__ __forceinline__ float to_float(double v) { return (float)v; }
+};
+template <> struct ZoneArith<ds> {
+    static __device__ __forceinline__ ds from_pair(float hi, float c) { return ds_fast(hi, -c); }
+    static __device__ __forceinline__ void to_pair(ds v, float &hi, float &c)
+    {
+        hi = v.hi;
+        c = -v.lo;
+    }
+    static __device__ __forceinline__ float to_float(ds v) { return v.hi; }
+};
+
 // Zone kernel of GRAY_FP32_KAHAN_SEL64: the rays of the hand-off list, in
-// double precision while r < r_demote (= r_promote + r_sw).  RETURN = true
+// extended precision T (double, or double-single on the single-precision
+// pipe: GRAY_ZONE_DS) while r < r_demote (= r_promote + r_sw).  RETURN = true
 // (first zone pass): double only; a ray that climbs out is stored as a
 // compensated single pair and appended to the return list R, which the next
 // single-precision pass drains at full occupancy (this kernel holds no
 // single-precision state and fits three blocks per SM).  RETURN = false (last
 // zone pass): a ray that climbs out continues in compensated single precision
 // here, switching back below r_promote, so every handed-off ray finishes.
-// The switches are exact one way (hi - lo to double) and a rounding the other
-// way (double to hi, lo), the same in both forms, so a ray's arithmetic does
-// not depend on which pass runs it.
-template <bool RETURN>
+// The switches are exact one way (hi - lo to T) and a rounding the other way
+// (T to hi, lo; exact for double-single), the same in both forms, so a ray's
+// arithmetic does not depend on which pass runs it.
+template <bool RETURN, typename T>
 __global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
 {
+    using Z = ZoneArith<T>;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const StateView &v = A.v;
-    StepOpt<double> Od;
-    Od.h_frac = A.h_frac;
-    Od.h_min = A.h_min;
-    Od.eps_xi = A.eps_xi;
+    StepOpt<T> Od;
+    Od.h_frac = T(A.h_frac);
+    Od.h_min = T(A.h_min);
+    Od.eps_xi = T(A.eps_xi);
     Od.eps_xi_d = A.eps_xi;
     Od.step_rule = A.step_rule;
     Od.stop_equator = A.stop_equator;
@@ -889,18 +913,19 @@ __global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
 
     bool has = false, exhausted = false, dbl = true;
     int64_t id = 0;
-    double yd[8], cz[8], find[4];
+    T yd[8], cz[8], find[4];
     float yf[8], cf[8], finf[4];
-    Hole<double> Hd;
+    Hole<T> Hd;
     Hole<float> Hf;
-    Geo<double> gd;
+    Geo<T> gd;
     Geo<float> gf;
-    double r_demote = INFINITY;
+    T r_demote = T(INFINITY);
+    const T r_sw = T(A.r_sw), cap_frac = T(A.cap_frac), r_esc_frac = T(A.r_esc_frac);
     int steps = 0, euler = 0, remaps = 0, n64 = 0, used = 0;
     unsigned long long tot_steps = 0, tot_euler = 0, tot_fp64 = 0;
 #pragma unroll
     for (int m = 0; m < 8; ++m)
-        cz[m] = 0.0;
+        cz[m] = T(0.0);
 
     for (;;) {
         const bool stop = cancelled(A, lane); // gray_cancel, as in trace32_kernel
@@ -931,25 +956,35 @@ __global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
                         remaps = s0.w;
                         n64 = s1.x;
                         used = (s1.y == epoch) ? s1.z : 0;
-                        const d4 p = ld_d4(v.P, my);
-                        Hd = make_hole(p.x, p.y, p.z, A.cap_frac, A.r_esc_frac, A.r_sw);
+                        if constexpr (sizeof(T) == 8 && !std::is_same<T, ds>::value) {
+                            const d4 p = ld_d4(v.P, my);
+                            Hd = make_hole(p.x, p.y, p.z, A.cap_frac, A.r_esc_frac, A.r_sw);
+                        } else {
+                            const float2 lows = *(const float2 *)&v.P[my].w;
+                            Hd = make_hole_ds(v.PF0[my], v.PF1[my], lows, cap_frac, r_esc_frac, r_sw);
+                        }
                         if (!RETURN)
                             Hf = make_hole_f(v.PF0[my], v.PF1[my], (float)A.cap_frac, (float)A.r_esc_frac,
                                              (float)A.r_sw);
-                        r_demote = Hd.r_promote + A.r_sw;
+                        r_demote = Hd.r_promote + r_sw;
                         if (s1.w & FLAG_DOUBLE_REPR) {
-                            // exact double state parked in the four single planes
+                            // exact double state parked in the four single planes (double zone)
                             const double2 q0 = ((const double2 *)v.X)[my], q1 = ((const double2 *)v.K)[my];
                             const double2 q2 = ((const double2 *)v.CX)[my], q3 = ((const double2 *)v.CK)[my];
-                            yd[0] = q0.x; yd[1] = q0.y; yd[2] = q1.x; yd[3] = q1.y;
-                            yd[4] = q2.x; yd[5] = q2.y; yd[6] = q3.x; yd[7] = q3.y;
+                            const double q[8] = {q0.x, q0.y, q1.x, q1.y, q2.x, q2.y, q3.x, q3.y};
+#pragma unroll
+                            for (int m = 0; m < 8; ++m) {
+                                float hi, c;
+                                ZoneArith<double>::to_pair(q[m], hi, c);
+                                yd[m] = std::is_same<T, ds>::value ? Z::from_pair(hi, c) : T(q[m]);
+                            }
                         } else {
                             const float4 X = ld_f4(v.X, my), K = ld_f4(v.K, my);
                             const float4 CX = ld_f4(v.CX, my), CK = ld_f4(v.CK, my);
-                            yd[0] = (double)X.x - CX.x; yd[1] = (double)X.y - CX.y;
-                            yd[2] = (double)X.z - CX.z; yd[3] = (double)X.w - CX.w;
-                            yd[4] = (double)K.x - CK.x; yd[5] = (double)K.y - CK.y;
-                            yd[6] = (double)K.z - CK.z; yd[7] = (double)K.w - CK.w;
+                            yd[0] = Z::from_pair(X.x, CX.x); yd[1] = Z::from_pair(X.y, CX.y);
+                            yd[2] = Z::from_pair(X.z, CX.z); yd[3] = Z::from_pair(X.w, CX.w);
+                            yd[4] = Z::from_pair(K.x, CK.x); yd[5] = Z::from_pair(K.y, CK.y);
+                            yd[6] = Z::from_pair(K.z, CK.z); yd[7] = Z::from_pair(K.w, CK.w);
                         }
                         gd = geometry(Hd, yd[1], yd[2]);
                     }
@@ -969,7 +1004,7 @@ __global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
                 if (steps >= A.max_steps) {
                     status = GRAY_RAY_STEP_CAP;
                     for (int m = 0; m < 4; ++m)
-                        find[m] = dbl ? yd[m] : (double)yf[m] - (double)cf[m];
+                        find[m] = dbl ? yd[m] : Z::from_pair(yf[m], cf[m]);
                 } else if (stop || (A.budget > 0 && used >= A.budget)) {
                     yield = true;
                 } else if (dbl && yd[1] >= r_demote) {
@@ -978,10 +1013,8 @@ __global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
                     if (RETURN) {
                         float hi[8], lo[8];
 #pragma unroll
-                        for (int m = 0; m < 8; ++m) {
-                            hi[m] = (float)yd[m];
-                            lo[m] = (float)((double)hi[m] - yd[m]);
-                        }
+                        for (int m = 0; m < 8; ++m)
+                            Z::to_pair(yd[m], hi[m], lo[m]);
                         st_f4(v.X, id, hi[0], hi[1], hi[2], hi[3]);
                         st_f4(v.K, id, hi[4], hi[5], hi[6], hi[7]);
                         st_f4(v.CX, id, lo[0], lo[1], lo[2], lo[3]);
@@ -992,10 +1025,8 @@ __global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
                         ret = true;
                     } else {
 #pragma unroll
-                        for (int m = 0; m < 8; ++m) {
-                            yf[m] = (float)yd[m];
-                            cf[m] = (float)((double)yf[m] - yd[m]);
-                        }
+                        for (int m = 0; m < 8; ++m)
+                            Z::to_pair(yd[m], yf[m], cf[m]);
                         gf = geometry(Hf, yf[1], yf[2], -cf[1], -cf[2]);
                         dbl = false;
                     }
@@ -1003,20 +1034,19 @@ __global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
                     stepped = false;
 #pragma unroll
                     for (int m = 0; m < 8; ++m)
-                        yd[m] = (double)yf[m] - (double)cf[m];
+                        yd[m] = Z::from_pair(yf[m], cf[m]);
                     gd = geometry(Hd, yd[1], yd[2]);
                     dbl = true;
                 } else {
                     const int e0 = euler;
                     if (RETURN || dbl) {
-                        status = step_once<double, false, true>(Hd, Od, yd, cz, gd, find, euler, remaps);
+                        status = step_once<T, false, true>(Hd, Od, yd, cz, gd, find, euler, remaps);
                         ++n64;
                         ++tot_fp64;
                     } else {
-                        status = step_once<float, true>(Hf, Of, yf, cf, gf, finf, euler, remaps, (const float2 *)&v.P[id].w,
-                                                     A.sincos_table);
+                        status = step_once<float, true>(Hf, Of, yf, cf, gf, finf, euler, remaps, (const float2 *)&v.P[id].w);
                         for (int m = 0; m < 4; ++m)
-                            find[m] = finf[m];
+                            find[m] = Z::from_pair(finf[m], 0.0f);
                     }
                     tot_euler += (unsigned long long)(euler - e0);
                     ++steps;
@@ -1025,26 +1055,36 @@ __global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
                 }
                 if (stepped && (status != GRAY_RAY_ACTIVE || yield)) {
                     int flags = 0;
-                    if (yield && dbl) {
-                        // park the exact double state; the ray resumes in double
-                        ((double2 *)v.X)[id] = make_double2(yd[0], yd[1]);
-                        ((double2 *)v.K)[id] = make_double2(yd[2], yd[3]);
-                        ((double2 *)v.CX)[id] = make_double2(yd[4], yd[5]);
-                        ((double2 *)v.CK)[id] = make_double2(yd[6], yd[7]);
-                        flags = FLAG_DOUBLE_MODE | FLAG_DOUBLE_REPR;
-                    } else {
+                    if constexpr (!std::is_same<T, ds>::value) {
+                        if (yield && dbl) {
+                            // park the exact double state; the ray resumes in double
+                            ((double2 *)v.X)[id] = make_double2(yd[0], yd[1]);
+                            ((double2 *)v.K)[id] = make_double2(yd[2], yd[3]);
+                            ((double2 *)v.CX)[id] = make_double2(yd[4], yd[5]);
+                            ((double2 *)v.CK)[id] = make_double2(yd[6], yd[7]);
+                            flags = FLAG_DOUBLE_MODE | FLAG_DOUBLE_REPR;
+                        }
+                    } else if (yield && dbl) {
+                        flags = FLAG_DOUBLE_MODE; // a double-single state is a compensated pair: stored below
+                    }
+                    if (!(flags & FLAG_DOUBLE_REPR)) {
                         float hi[8], lo[8];
 #pragma unroll
                         for (int m = 0; m < 8; ++m) {
-                            hi[m] = dbl ? (float)yd[m] : yf[m];
-                            lo[m] = dbl ? (float)((double)hi[m] - yd[m]) : cf[m];
+                            if (dbl) {
+                                Z::to_pair(yd[m], hi[m], lo[m]);
+                            } else {
+                                hi[m] = yf[m];
+                                lo[m] = cf[m];
+                            }
                         }
                         st_f4(v.X, id, hi[0], hi[1], hi[2], hi[3]);
                         st_f4(v.K, id, hi[4], hi[5], hi[6], hi[7]);
                         st_f4(v.CX, id, lo[0], lo[1], lo[2], lo[3]);
                         st_f4(v.CK, id, lo[4], lo[5], lo[6], lo[7]);
                         if (status != GRAY_RAY_ACTIVE)
-                            st_f4(v.F, id, (float)find[0], (float)find[1], (float)find[2], (float)find[3]);
+                            st_f4(v.F, id, Z::to_float(find[0]), Z::to_float(find[1]), Z::to_float(find[2]),
+                                  Z::to_float(find[3]));
                     }
                     v.S0[id] = make_int4(status, steps, euler, remaps);
                     v.S1[id] = make_int4(n64, epoch, used, flags);
@@ -1688,26 +1728,12 @@ __global__ void splat_kernel(StateView v, int prec, int64_t first, int64_t n, Ca
     deposit<T>(c, px, py, z, count, depth);
 }
 
-// The sin/cos table of the double-single Eq. 4 re-test: sin and cos of j/32,
-// j in [-256, 256), each as the two floats nearest to the double value and
-// to its remainder (computed in double, ~2^-48 relative after the split).
-__global__ void sincos_table_kernel(float4 *table)
-{
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= 2 * SINCOS_TABLE_HALF)
-        return;
-    double s, c;
-    sincos((double)(k - SINCOS_TABLE_HALF) * 0.03125, &s, &c);
-    const float sh = (float)s, ch = (float)c;
-    table[k] = make_float4(sh, (float)(s - (double)sh), ch, (float)(c - (double)ch));
-}
-
 // --------------------------------------------------------------------------
 // Unit evaluations for parity tests
 // --------------------------------------------------------------------------
 
 template <typename T>
-__global__ void eval_kernel(int what, const double *in, int64_t n, double *out, const float4 *sincos_table)
+__global__ void eval_kernel(int what, const double *in, int64_t n, double *out)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
@@ -1748,7 +1774,7 @@ __global__ void eval_kernel(int what, const double *in, int64_t n, double *out, 
     } else if (what == GRAY_EVAL_SINCOS_DS) {
         if constexpr (sizeof(T) == 4) {
             ds sv, cv;
-            ds_sincos((float)in[i], sincos_table, sv, cv);
+            ds_sincos((float)in[i], sv, cv);
             out[2 * i] = (double)sv.hi + (double)sv.lo;
             out[2 * i + 1] = (double)cv.hi + (double)cv.lo;
         }
@@ -1772,13 +1798,13 @@ __global__ void eval_kernel(int what, const double *in, int64_t n, double *out, 
             const NormF nf = null_norm_f(H, g, y1);
             const float4 aM = make_float4(H.a, (float)(a - (double)(float)a), H.M, (float)(M - (double)(float)M));
             float iS;
-            const ds nd = null_norm_ds(y1, c1, aM, sincos_table, iS);
+            const ds nd = null_norm_ds(y1, c1, aM, iS);
             out[6 * i] = (double)nd.hi + (double)nd.lo;
             out[6 * i + 1] = (double)nf.norm;
             out[6 * i + 2] = (double)nf.size;
             out[6 * i + 3] = amb ? 1.0 : 0.0;
             out[6 * i + 4] = redo ? 1.0 : 0.0;
-            out[6 * i + 5] = xi_fails_ds(y1, c1, aM, sincos_table, eps) ? 1.0 : 0.0;
+            out[6 * i + 5] = xi_fails_ds(y1, c1, aM, eps) ? 1.0 : 0.0;
         }
     } else if (what == GRAY_EVAL_XI) {
         const double *q = in + 10 * i;
@@ -1831,6 +1857,34 @@ template <typename T> __global__ void fma_peak_kernel(int64_t iters, T *sink)
 
 int cuda_err(cudaError_t e) { return e == cudaSuccess ? GRAY_OK : GRAY_ECUDA; }
 
+// The constant table of ds_sincos on the current device, filled once per
+// device (from the host: sin and cos of j/32 in double, split into the
+// nearest float and the float nearest to the remainder).  A synchronous copy,
+// so every later launch sees it; done at context creation (before any
+// stream capture) and by gray_eval.
+constexpr int kMaxTableDevices = 256;
+std::atomic<int> g_sincos_table_ready[kMaxTableDevices];
+
+int ensure_sincos_table()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxTableDevices)
+        return GRAY_ECUDA;
+    if (g_sincos_table_ready[dev].load(std::memory_order_acquire))
+        return GRAY_OK;
+    float4 t[2 * SINCOS_TABLE_HALF];
+    for (int k = 0; k < 2 * SINCOS_TABLE_HALF; ++k) {
+        const double x = (double)(k - SINCOS_TABLE_HALF) * 0.03125;
+        const double sv = std::sin(x), cv = std::cos(x);
+        const float sh = (float)sv, ch = (float)cv;
+        t[k] = make_float4(sh, (float)(sv - (double)sh), ch, (float)(cv - (double)ch));
+    }
+    if (cudaMemcpyToSymbol(c_sincos_table, t, sizeof t) != cudaSuccess)
+        return GRAY_ECUDA;
+    g_sincos_table_ready[dev].store(1, std::memory_order_release);
+    return GRAY_OK;
+}
+
 int check_launch()
 {
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -1862,6 +1916,8 @@ int validate_options(const gray_options *o)
     if (o->launch != GRAY_LAUNCH_PERSISTENT && o->launch != GRAY_LAUNCH_ONE_PER_THREAD)
         return GRAY_EINVAL;
     if (o->stop_equator != 0 && o->stop_equator != 1)
+        return GRAY_EINVAL;
+    if ((o->zone_arith != GRAY_ZONE_DS && o->zone_arith != GRAY_ZONE_FP64) || o->reserved != 0)
         return GRAY_EINVAL;
     if (!finite_all({o->h_frac, o->h_min, o->cap_frac, o->eps_xi, o->r_esc_frac, o->r_sw}))
         return GRAY_EINVAL;
@@ -1977,6 +2033,7 @@ void gray_default_options(gray_options *o)
     o->blocks_per_sm = 0;
     o->refill = 0;
     o->launch = GRAY_LAUNCH_PERSISTENT;
+    o->zone_arith = GRAY_ZONE_DS;
     o->h_frac = 1.0 / 32.0;
     o->h_min = 1e-3;
     o->cap_frac = 1.01;
@@ -2032,14 +2089,7 @@ int gray_create(gray_ctx **ctx, const gray_options *opt)
         gray_destroy(c);
         return GRAY_ECUDA;
     }
-    if (cudaMalloc((void **)&c->sincos_table, 2 * SINCOS_TABLE_HALF * sizeof(float4)) != cudaSuccess) {
-        gray_destroy(c);
-        return GRAY_ENOMEM;
-    }
-    // filled once, on the legacy stream, and waited for: every later call of
-    // the context (on any stream, or captured in a graph) finds it ready
-    sincos_table_kernel<<<2 * SINCOS_TABLE_HALF / 128, 128>>>(c->sincos_table);
-    if (check_launch() != GRAY_OK || cudaStreamSynchronize(0) != cudaSuccess) {
+    if (ensure_sincos_table() != GRAY_OK) {
         gray_destroy(c);
         return GRAY_ECUDA;
     }
@@ -2063,7 +2113,6 @@ void gray_destroy(gray_ctx *ctx)
         cudaStreamDestroy(ctx->side);
     cudaFree(ctx->ws);
     cudaFree(ctx->aux);
-    cudaFree(ctx->sincos_table);
     if (ctx->cancel_stream)
         cudaStreamDestroy(ctx->cancel_stream);
     cudaFreeHost(ctx->ws_host);
@@ -2142,7 +2191,6 @@ TraceArgs make_trace_args(gray_ctx *ctx, void *state, int64_t n_state, int64_t s
     A.r_esc_frac = o.r_esc_frac;
     A.r_sw = o.r_sw;
     A.ws = ctx->ws;
-    A.sincos_table = ctx->sincos_table;
     A.cancel = (const int *)&ctx->aux[AUX_CANCEL];
     A.one_per_thread = o.launch == GRAY_LAUNCH_ONE_PER_THREAD;
     A.stop_equator = o.stop_equator;
@@ -2269,7 +2317,10 @@ int gray_trace(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, 
             // each draining many zone rays, waste the fewest pipe cycles on
             // partly filled warps (measured: 1.95 ms at three blocks per SM,
             // 1.53 ms at one, 2.2 ms with 64-thread blocks)
-            zone_kernel<true><<<(unsigned)ctx->num_sms, block, 0, s>>>(Z);
+            if (ctx->opt.zone_arith == GRAY_ZONE_FP64)
+                zone_kernel<true, double><<<(unsigned)ctx->num_sms, block, 0, s>>>(Z);
+            else
+                zone_kernel<true, ds><<<(unsigned)ctx->num_sms, block, 0, s>>>(Z);
             if ((rc = check_launch()))
                 return rc;
             // the hand-off list is consumed: pass B appends to it from 0
@@ -2281,8 +2332,12 @@ int gray_trace(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, 
             if (cudaMemsetAsync(&ctx->ws->head, 0, sizeof(unsigned long long), s) != cudaSuccess)
                 return GRAY_ECUDA;
             Z.zone_return = 0;
-            zone_kernel<false>
-                <<<persistent_grid(ctx, (const void *)zone_kernel<false>, block, work), block, 0, s>>>(Z);
+            if (ctx->opt.zone_arith == GRAY_ZONE_FP64)
+                zone_kernel<false, double>
+                    <<<persistent_grid(ctx, (const void *)zone_kernel<false, double>, block, work), block, 0, s>>>(Z);
+            else
+                zone_kernel<false, ds>
+                    <<<persistent_grid(ctx, (const void *)zone_kernel<false, ds>, block, work), block, 0, s>>>(Z);
             if ((rc = check_launch()))
                 return rc;
             if (ctx->timing)
@@ -2792,22 +2847,14 @@ int gray_eval(int32_t what, int32_t precision, const double *in, int64_t n, doub
         return GRAY_OK;
     if (!in || !out)
         return GRAY_EINVAL;
-    cudaStream_t s = (cudaStream_t)stream;
-    if (precision == GRAY_FP64) {
-        eval_kernel<double><<<grid_for(n, 128), 128, 0, s>>>(what, in, n, out, nullptr);
-        return check_launch();
-    }
-    float4 *table = nullptr;
-    if (cudaMallocAsync((void **)&table, 2 * SINCOS_TABLE_HALF * sizeof(float4), s) != cudaSuccess)
+    if (ensure_sincos_table() != GRAY_OK)
         return GRAY_ECUDA;
-    sincos_table_kernel<<<2 * SINCOS_TABLE_HALF / 128, 128, 0, s>>>(table);
-    int rc = check_launch();
-    if (!rc) {
-        eval_kernel<float><<<grid_for(n, 128), 128, 0, s>>>(what, in, n, out, table);
-        rc = check_launch();
-    }
-    cudaFreeAsync(table, s);
-    return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == GRAY_FP64)
+        eval_kernel<double><<<grid_for(n, 128), 128, 0, s>>>(what, in, n, out);
+    else
+        eval_kernel<float><<<grid_for(n, 128), 128, 0, s>>>(what, in, n, out);
+    return check_launch();
 }
 
 int gray_fma_peak(int32_t precision, int32_t blocks, int32_t threads, int64_t iters, void *sink, size_t sink_bytes,

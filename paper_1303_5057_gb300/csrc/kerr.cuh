@@ -527,6 +527,10 @@ __device__ __forceinline__ bool xi_fails_flag(const Hole<float> &H, const Geo<fl
 // (GB300's FP64 rate is 1/64 of FP32's).
 struct ds {
     float hi, lo;
+    ds() = default;
+    __host__ __device__ constexpr ds(float h, float l) : hi(h), lo(l) {}
+    // from a double constant (folded at compile time for literals)
+    __host__ __device__ constexpr explicit ds(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
 };
 __device__ __forceinline__ ds ds_two_sum(float a, float b)
 {
@@ -563,25 +567,61 @@ __device__ __forceinline__ ds ds_mulf(ds x, float y)
 // r + r (1 - x r) whose residual 1 - x r is formed exactly.
 __device__ __forceinline__ ds ds_recip(ds x)
 {
-    const float r = 1.0f / x.hi;
+    const float r = recip(x.hi);
     const ds xr = ds_mulf(x, r);
     const float e = (1.0f - xr.hi) - xr.lo;
     return ds_fast(r, r * e);
 }
 
+// ---- double-single as a number type ---------------------------------------
+// (the library's float and double overloads stay visible next to these)
+using ::fabs;
+using ::fma;
+using ::fmax;
+using ::fmin;
+// The arithmetic the templated tracer functions need (step size, right-hand
+// side, RK4, Eq. 4, Eq. 3, stop tests), so that the steps near the horizon
+// can run in double-single on the single-precision pipe instead of in double
+// (GB300's FP64 pipe runs at 1/64 of the FP32 rate).  Values are kept
+// normalised (|lo| <= ulp(hi)/2); comparisons order by hi, then lo.
+__device__ __forceinline__ ds operator+(ds a, ds b) { return ds_add(a, b); }
+__device__ __forceinline__ ds operator-(ds a) { return ds_neg(a); }
+__device__ __forceinline__ ds operator-(ds a, ds b) { return ds_add(a, ds_neg(b)); }
+__device__ __forceinline__ ds operator*(ds a, ds b) { return ds_mul(a, b); }
+__device__ __forceinline__ ds operator/(ds a, ds b) { return ds_mul(a, ds_recip(b)); }
+__device__ __forceinline__ bool operator<(ds a, ds b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool operator>(ds a, ds b) { return b < a; }
+__device__ __forceinline__ bool operator<=(ds a, ds b) { return !(b < a) && a.hi == a.hi && b.hi == b.hi; }
+__device__ __forceinline__ bool operator>=(ds a, ds b) { return b <= a; }
+__device__ __forceinline__ ds fma(ds a, ds b, ds c) { return ds_add(ds_mul(a, b), c); }
+__device__ __forceinline__ ds fabs(ds a) { return a.hi < 0.0f ? ds_neg(a) : a; }
+__device__ __forceinline__ ds fmin(ds a, ds b) { return b < a ? b : a; }
+__device__ __forceinline__ ds fmax(ds a, ds b) { return a < b ? b : a; }
+__device__ __forceinline__ ds recip(ds a) { return ds_recip(a); }
+__device__ __forceinline__ ds recip_approx(ds a) { return ds_recip(a); }
+template <> __device__ __forceinline__ ds pi_v<ds>() { return ds(3.14159265358979323846); }
+__device__ __forceinline__ bool finite_v(float x) { return isfinite(x); }
+__device__ __forceinline__ bool finite_v(double x) { return isfinite(x); }
+__device__ __forceinline__ bool finite_v(ds x) { return isfinite(x.hi) && isfinite(x.lo); }
+
 // sin and cos of a float angle x (|x| < 8) in double-single, from a table
-// of sin and cos at the multiples x0 = j/32 (each as two floats, made in
-// double by sincos_table_kernel) and angle addition: d = x - x0 is exact,
-// |d| <= 1/64, and sin d = d - d^3/6 + d^5/120, cos d = 1 - d^2/2 + d^4/24
-// (truncation below 2e-15) need double-single only for d and d^2.
+// of sin and cos at the multiples x0 = j/32 (each as the two floats nearest to
+// the double value and to its remainder, filled from the host once per
+// device) and angle addition: d = x - x0 is exact, |d| <= 1/64, and
+// sin d = d - d^3/6 + d^5/120, cos d = 1 - d^2/2 + d^4/24 (truncation below
+// 2e-15) need double-single only for d and d^2.  j comes from the 1.5 * 2^23
+// rounding addition: no float-integer conversion.
 constexpr int SINCOS_TABLE_HALF = 256; // entries j/32 for j in [-256, 256)
-__device__ __forceinline__ void ds_sincos(float x, const float4 *table, ds &s, ds &c)
+__constant__ float4 c_sincos_table[2 * SINCOS_TABLE_HALF];
+__device__ __forceinline__ void ds_sincos(float x, ds &s, ds &c)
 {
-    int j = (int)rintf(x * 32.0f);
+    const float t = fmaf(x, 32.0f, 12582912.0f);
+    const float jf = t - 12582912.0f;
+    int j = __float_as_int(t) - 0x4B400000; // jf as an integer
     j = j < -SINCOS_TABLE_HALF ? -SINCOS_TABLE_HALF : (j > SINCOS_TABLE_HALF - 1 ? SINCOS_TABLE_HALF - 1 : j);
-    const float4 t = table[j + SINCOS_TABLE_HALF];
-    const ds S0{t.x, t.y}, C0{t.z, t.w};
-    const float d = x - (float)j * 0.03125f; // exact
+    const float4 e = c_sincos_table[j + SINCOS_TABLE_HALF];
+    const ds S0{e.x, e.y}, C0{e.z, e.w};
+    const float d = fmaf(-jf, 0.03125f, x); // exact
     const float p = d * d, pe = fmaf(d, d, -p); // d^2 = p + pe exactly
     const ds sd = ds_fast(d, d * p * fmaf(p, 1.0f / 120.0f, -1.0f / 6.0f));
     const ds cd = ds_add(ds{1.0f, 0.0f}, ds{-0.5f * p, fmaf(p * p, 1.0f / 24.0f, -0.5f * pe)});
@@ -589,21 +629,44 @@ __device__ __forceinline__ void ds_sincos(float x, const float4 *table, ds &s, d
     c = ds_add(ds_mul(C0, cd), ds_neg(ds_mul(S0, sd)));
 }
 
+// sin and cos of a double-single angle (|x| < 8): ds_sincos of the high
+// word, then the first-order term of the low one (|lo| <= 2^-24 |x|).
+__device__ __forceinline__ void fsincos(ds x, ds *s, ds *c)
+{
+    ds s0, c0;
+    ds_sincos(x.hi, s0, c0);
+    *s = ds_add(s0, ds{c0.hi * x.lo, 0.0f});
+    *c = ds_add(c0, ds{-s0.hi * x.lo, 0.0f});
+}
+
+// sin and cos of a small double-single angle d (|d| <= 1/64, the stage
+// increments near the horizon) by their series: d and -d^2/2 in
+// double-single, the smaller terms in single precision (truncation below
+// 1e-17).  Returns false for larger |d|.
+__device__ __forceinline__ bool small_sincos(ds d, ds *s, ds *c)
+{
+    if (!(fabsf(d.hi) <= 0.015625f))
+        return false;
+    const float p = d.hi * d.hi;
+    *s = ds_add(d, ds{d.hi * p * fmaf(p, fmaf(p, -1.0f / 5040.0f, 1.0f / 120.0f), -1.0f / 6.0f), 0.0f});
+    const ds d2 = ds_mul(d, d);
+    *c = ds_add(ds{1.0f, 0.0f}, ds{-0.5f * d2.hi, fmaf(p * p, fmaf(p, -1.0f / 720.0f, 1.0f / 24.0f), -0.5f * d2.lo)});
+    return true;
+}
+
 // The null norm g(k, k) in double-single arithmetic of a compensated
 // single-precision state (the true state is hi - lo: y1 the high words, c1
 // the low ones) with the spin and mass split into two floats each, aM =
-// (a_hi, a_lo, M_hi, M_lo) and the sin/cos table of ds_sincos: accurate to
-// ~2^-40 of its terms, where single precision resolves ~2^-21.  Also returns
-// 1/Sigma (high word).
-__device__ __forceinline__ ds null_norm_ds(const float *y1, const float *c1, float4 aM, const float4 *table,
-                                         float &iS_hi)
+// (a_hi, a_lo, M_hi, M_lo): accurate to ~2^-40 of its terms, where single
+// precision resolves ~2^-21.  Also returns 1/Sigma (high word).
+__device__ __forceinline__ ds null_norm_ds(const float *y1, const float *c1, float4 aM, float &iS_hi)
 {
     const ds r = ds_fast(y1[1], -c1[1]);
     const ds kt = ds_fast(y1[4], -c1[4]), kr = ds_fast(y1[5], -c1[5]);
     const ds kh = ds_fast(y1[6], -c1[6]), kp = ds_fast(y1[7], -c1[7]);
     const ds a = ds_fast(aM.x, aM.y), M = ds_fast(aM.z, aM.w);
     ds s, c;
-    ds_sincos(y1[2], table, s, c);
+    ds_sincos(y1[2], s, c);
     // sin and cos of theta_hi - theta_lo to first order in the low word
     const float tl = c1[2];
     const ds sn = ds_add(s, ds{-c.hi * tl, 0.0f});
@@ -623,11 +686,10 @@ __device__ __forceinline__ ds null_norm_ds(const float *y1, const float *c1, flo
 // The Eq. 4 test re-taken in double-single arithmetic: |g(k, k)| of
 // null_norm_ds against eps |g_tt (k^t)^2|.  The threshold needs no such care:
 // single precision forms it to ~2^-23 of itself.
-__device__ __forceinline__ bool xi_fails_ds(const float *y1, const float *c1, float4 aM, const float4 *table,
-                                            float eps)
+__device__ __forceinline__ bool xi_fails_ds(const float *y1, const float *c1, float4 aM, float eps)
 {
     float iS;
-    const ds norm = null_norm_ds(y1, c1, aM, table, iS);
+    const ds norm = null_norm_ds(y1, c1, aM, iS);
     const float r = y1[1] - c1[1], kt = y1[4] - c1[4];
     const float gtt = fmaf(-2.0f * aM.z * r, iS, 1.0f);
     return !(fabsf(norm.hi + norm.lo) <= eps * fabsf(gtt * (kt * kt)));
@@ -796,6 +858,72 @@ __device__ __noinline__ void stop_surface_mixed(const double *y0, const double *
         fin[2] = -fin[2];
         fin[3] = fin[3] - pi_v<double>();
     }
+}
+
+// The same for double-single steps (the zone tracer's default arithmetic):
+// offsets in double-single, crossing and Hermite increments in single
+// precision, added back in double-single.
+__device__ __noinline__ void stop_surface_mixed(const ds *y0, const ds *y1, ds h, ds r_stop, ds *fin)
+{
+    float z0[8], z1[8];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        z0[m] = 0.0f;
+        z1[m] = (y1[m] - y0[m]).hi;
+        z0[4 + m] = y0[4 + m].hi;
+        z1[4 + m] = y1[4 + m].hi;
+    }
+    const float hf = h.hi;
+    const float sf = crossing_fraction<float>(z0, z1, hf, (r_stop - y0[1]).hi);
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        fin[m] = y0[m] + ds{hermite<float>(0.0f, z0[4 + m], z1[m], z1[4 + m], hf, sf), 0.0f};
+    if (fin[2] > pi_v<ds>()) {
+        fin[2] = ds(2.0) * pi_v<ds>() - fin[2];
+        fin[3] = fin[3] + pi_v<ds>();
+    } else if (fin[2] < ds(0.0)) {
+        fin[2] = -fin[2];
+        fin[3] = fin[3] - pi_v<ds>();
+    }
+}
+
+// Per-ray constants in double-single from the single-precision planes
+// (PF0: a, M, r_+ high, r_+ low; PF1: r_-, dc, r_h, r_obs) and the low
+// words of a and M (the fourth slot of P): r_- = 2M - r_+ and dc = 0 below
+// extremal spin, the surfaces from the double options.
+__device__ __forceinline__ Hole<ds> make_hole_ds(float4 c0, float4 c1, float2 lows, ds cap_frac, ds r_esc_frac,
+                                                 ds r_sw)
+{
+    Hole<ds> H;
+    H.a = ds_fast(c0.x, lows.x);
+    H.M = ds_fast(c0.y, lows.y);
+    H.a2 = H.a * H.a;
+    H.Ma = H.M * H.a;
+    H.m2M = ds(-2.0) * H.M;
+    H.t2a = ds(2.0) * H.a;
+    H.t2a2 = ds(2.0) * H.a2;
+    H.t2Ma = ds(2.0) * H.Ma;
+    H.rp = ds_fast(c0.z, c0.w);
+    H.rp_lo = ds(0.0);
+    if (c1.y > 0.0f) { // |a| > M: no horizon roots (Delta = (r - M)^2 + a^2 - M^2)
+        H.rp = H.M;
+        H.rm = H.M;
+        H.dc = H.a2 - H.M * H.M;
+    } else {
+        H.rm = ds(2.0) * H.M - H.rp;
+        H.dc = ds(0.0);
+    }
+    if (c0.y > 0.0f) {
+        H.r_h = H.rp;
+        H.r_cap = cap_frac * H.rp;
+        H.r_promote = H.r_cap + r_sw;
+    } else {
+        H.r_h = ds(-INFINITY, 0.0f);
+        H.r_cap = ds(-1.0);
+        H.r_promote = ds(-INFINITY, 0.0f);
+    }
+    H.r_esc = r_esc_frac * ds(c1.w, 0.0f);
+    return H;
 }
 
 // Image-plane initial conditions in double precision: flat-space picture of

@@ -28,6 +28,7 @@ RENDER_PIXELS64, RENDER_PIXELS32, RENDER_RECORD, RENDER_INVARIANTS = 0, 1, 3, 4
 EVAL_CHRISTOFFEL, EVAL_RHS, EVAL_INITIAL, EVAL_XI, EVAL_SINCOS, EVAL_RECIP = 0, 1, 2, 3, 4, 5
 EVAL_SINCOS_DS, EVAL_NORM = 6, 7
 LAUNCH_PERSISTENT, LAUNCH_ONE_PER_THREAD = 0, 1
+ZONE_DS, ZONE_FP64 = 0, 1
 GRID_CARTESIAN, GRID_POLAR = 0, 1
 RECORD = 17
 NOALLOC_MAX_IMAGES = 4096
@@ -45,6 +46,7 @@ class _Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("step_rule", C.c_int32), ("max_steps", C.c_int32),
                 ("block", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill", C.c_int32),
                 ("launch", C.c_int32), ("stop_equator", C.c_int32),
+                ("zone_arith", C.c_int32), ("reserved", C.c_int32),
                 ("h_frac", C.c_double), ("h_min", C.c_double), ("cap_frac", C.c_double),
                 ("eps_xi", C.c_double), ("r_esc_frac", C.c_double), ("r_sw", C.c_double)]
 
@@ -103,6 +105,8 @@ class Options:
     refill: int = 0
     launch: int = LAUNCH_PERSISTENT
     stop_equator: int = 0
+    zone_arith: int = 0  # ZONE_DS
+    reserved: int = 0
     h_frac: float = 1.0 / 32.0
     h_min: float = 1e-3
     cap_frac: float = 1.01
