@@ -40,21 +40,24 @@ UNIT = "photon-steps/s"
 F_STEP = 559
 F_KAHAN = 32
 # Special-function work per step: one full sin/cos (the step's end point), three
-# by angle addition with short series (the interior stages, no SFU), and about
-# seven SFU reciprocals (one per geometry, plain; one or two in the step size,
-# refined by a Newton-Raphson step); ncu puts the SFU pipe at ~6 % busy.  At
-# 16 SFU results per clock per SM the reciprocals alone would allow
-# 152 x 16 x 2.070e9 / 7 = 7.2e11 steps/s, far above the FMA bound.
-SPECIAL_PER_STEP = {"sincos_full": 1, "sincos_by_angle_addition": 3, "sfu_reciprocal": 7}
+# by angle addition with short series (the interior stages, no SFU), and 13
+# SFU reciprocals (three per geometry, plain, for four geometries; one in the
+# step size, refined by a Newton-Raphson step), three more on a redone step.
+# At 16 SFU results per clock per SM they alone would allow
+# 152 x 16 x 2.070e9 / 13 = 3.9e11 steps/s, far above the FMA bound.
+SPECIAL_PER_STEP = {"sincos_full": 1, "sincos_by_angle_addition": 3, "sfu_reciprocal": 13}
 SFU_PER_CLK_PER_SM = 16
 # Nominal FP32 non-tensor peak: 152 SMs x 128 FP32 lanes x 2 flop/FMA x
 # 2.070 GHz (context; the roofline divides by the rate measured in the run).
 SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.070
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1000.0
 # DRAM bytes (read + write) of one launch of the dominant kernel (the
-# single-precision pass of this workload) from an ncu capture of that
-# kernel; None until counters of the current kernel are taken.
-TRAFFIC_BYTES = None
+# single-precision pass of the 1024^2 image, planned queue), from ncu's
+# dram__bytes_read.sum + dram__bytes_write.sum (one pass, full size):
+# 1.42e8 read + 0.64e8 written.  The pass moves ~250 B per ray (state, stop
+# point, status, per-ray constants, queue entry); part of what the set-up
+# just wrote is still in L2.
+TRAFFIC_BYTES = 2.06e8
 # Nominal FP64 non-tensor peak at 2 FP64 lanes per SM (context only).
 FP64_PEAK_TFLOPS = SMS * 2 * 2 * SM_MAX_GHZ / 1000.0
 
@@ -100,7 +103,7 @@ def parse_args():
                    help="skip the FMA-chain peak measurement (the roofline then divides by the nominal peaks)")
     p.add_argument("--serve-rates", default="10,30", help="serving leg: Poisson arrival rates (req/s)")
     p.add_argument("--serve-seconds", type=float, default=20.0, help="serving leg: seconds of arrivals per rate")
-    p.add_argument("--serve-saturation", type=int, default=80,
+    p.add_argument("--serve-saturation", type=int, default=240,
                    help="serving leg: requests offered at once to measure the saturated rate (0: skip)")
     return p.parse_args()
 

@@ -641,7 +641,6 @@ template <int MODE> __global__ void __maxnreg__(128) trace32_kernel(TraceArgs A)
     O.h_frac = (float)A.h_frac;
     O.h_min = (float)A.h_min;
     O.eps_xi = (float)A.eps_xi;
-    O.eps_xi_d = A.eps_xi;
     O.step_rule = A.step_rule;
     O.stop_equator = A.stop_equator;
 
@@ -798,7 +797,6 @@ __global__ void __launch_bounds__(128) trace64_kernel(TraceArgs A)
     O.h_frac = A.h_frac;
     O.h_min = A.h_min;
     O.eps_xi = A.eps_xi;
-    O.eps_xi_d = A.eps_xi;
     O.step_rule = A.step_rule;
     O.stop_equator = A.stop_equator;
 
@@ -937,14 +935,12 @@ __global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
     Od.h_frac = T(A.h_frac);
     Od.h_min = T(A.h_min);
     Od.eps_xi = T(A.eps_xi);
-    Od.eps_xi_d = A.eps_xi;
     Od.step_rule = A.step_rule;
     Od.stop_equator = A.stop_equator;
     StepOpt<float> Of;
     Of.h_frac = (float)A.h_frac;
     Of.h_min = (float)A.h_min;
     Of.eps_xi = (float)A.eps_xi;
-    Of.eps_xi_d = A.eps_xi;
     Of.step_rule = A.step_rule;
     Of.stop_equator = A.stop_equator;
     const int64_t n = (int64_t)*(volatile unsigned long long *)&A.ws->handoff;

@@ -93,7 +93,6 @@ template <typename T> struct Hole {
 // Integration options used inside a step.
 template <typename T> struct StepOpt {
     T h_frac, h_min, eps_xi;
-    double eps_xi_d;  // eps_xi in double, for the double confirmation of ambiguous single-precision tests
     int step_rule;    // 0: benchmark rule, 1: Eq. 2
     int stop_equator; // 1: stop at the first crossing of theta = pi/2 (Sec. 3 projection)
 };
@@ -307,20 +306,31 @@ __device__ __forceinline__ float recip_approx(float x)
 __device__ __forceinline__ double recip_approx(double x) { return recip(x); }
 
 // Geometry of one point (r, theta): the quantities every right-hand side and
-// the Eq. 4 monitor need.  The three reciprocals come from one reciprocal of
-// Sigma Delta sin(theta).
+// the Eq. 4 monitor need, with the reciprocals of Sigma, Delta and sin(theta).
 template <typename T> struct Geo {
     T r, s, c, Sigma, Delta, iS, iD, is;
 };
 
-// 1/Sigma, 1/Delta and 1/sin from one reciprocal of Sigma Delta sin.
+// 1/Sigma, 1/Delta and 1/sin.  Single precision: three hardware
+// reciprocals, one issue slot each (they run on the SFU pipe, beside the
+// FMA pipe), each within 2 ulp (unit test); forming the three from one
+// reciprocal of Sigma Delta sin takes eight issue slots and rounds up to
+// five times (single-precision pass 8.33 -> 8.00 ms on the 1024^2 image).
+// Double and double-single keep the one reciprocal (there each reciprocal
+// is a refined sequence).
 template <typename T> __device__ __forceinline__ void geometry_reciprocals(Geo<T> &g)
 {
-    const T Ds = g.Delta * g.s, SD = g.Sigma * g.Delta;
-    const T inv = recip_approx(SD * g.s);
-    g.iS = inv * Ds;
-    g.iD = inv * (g.Sigma * g.s);
-    g.is = inv * SD;
+    if constexpr (sizeof(T) == 4) {
+        g.iS = recip_approx(g.Sigma);
+        g.iD = recip_approx(g.Delta);
+        g.is = recip_approx(g.s);
+    } else {
+        const T Ds = g.Delta * g.s, SD = g.Sigma * g.Delta;
+        const T inv = recip_approx(SD * g.s);
+        g.iS = inv * Ds;
+        g.iD = inv * (g.Sigma * g.s);
+        g.is = inv * SD;
+    }
 }
 
 // dr and dth are the low words of a compensated single-precision point (the
