@@ -759,7 +759,11 @@ def main():
             "steps_per_pass": steps_per_pass, "fp64_steps_per_pass": fp64_steps,
             "setup_plan_ms": statistics.mean(setup_plan_ms), "trace_ms": statistics.mean(trace_ms),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": achieved / fp32_peak, "traffic": TRAFFIC_BYTES,
+                         "frac": achieved / fp32_peak,
+                         # the captured figure belongs to the default workload only
+                         "traffic": TRAFFIC_BYTES if (args.side == 1024 and not args.no_plan
+                                                      and args.precision == "fp32_kahan_sel64"
+                                                      and args.step_rule == "bench" and args.r_sw == 0.02) else None,
                          "kernel": "trace32_kernel (single-precision pass)", "kernel_ms": main_ms,
                          "kernel_steps": main_pass_steps,
                          "peak_source": ("measured: FP32 FMA chains (gray_fma_peak) in this run, at the SM clock in "
