@@ -148,12 +148,14 @@ class Reference:
         return len(self.rays)
 
     def done(self):
+        """Rays the oracle traces to a stop surface: capture, escape, or the
+        equatorial plane of the Sec. 3 projection."""
         st = self.ref[:, 0]
-        return (st == oracle.CAPTURED) | (st == oracle.ESCAPED)
+        return (st == oracle.CAPTURED) | (st == oracle.ESCAPED) | (st == oracle.EQUATOR)
 
     def faithful(self):
         """Rays outside the band that are neither chaotic nor diverged, and
-        that the oracle traces to capture or escape."""
+        that the oracle traces to a stop surface."""
         return self.far & ~self.chaotic & ~self.diverged & self.done()
 
     def compared(self, precision="single"):

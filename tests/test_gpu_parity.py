@@ -281,12 +281,17 @@ def test_grid_projection_matches_oracle(a, incl_deg):
     assert np.all(rec64[eq, 6] == np.float64(math.pi / 2))
     rec32, _, _, _ = trace_image(im, gray.Options(precision=gray.FP32_KAHAN_SEL64, max_steps=20000, r_sw=0.02,
                                                   stop_equator=1))
-    same32 = (rec32[:, 0] == ref[:, 0]) & far
-    assert same32.sum() >= 0.9999 * far.sum()
-    eq32 = same32 & (ref[:, 0] == oracle.EQUATOR)
-    rel = np.abs(rec32[eq32, 5] - ref[eq32, 5]) / ref[eq32, 5]
-    assert np.percentile(rel, 99) < 1e-4
-    assert np.percentile(np.abs(P.wrap(rec32[eq32, 7] - ref[eq32, 7])), 99) < 1e-4
+    # single precision: every ray outside the band that the oracle resolves
+    # (not chaotic, and its crossing conditioned at single precision, as in
+    # the acceptance tests) keeps its status, crossing radius and phi
+    R = P.Reference(rays, oracle.Options(max_steps=20000, stop_equator=1), far)
+    settled = far & ~R.chaotic
+    assert np.all(rec32[settled, 0] == ref[settled, 0])
+    sel = R.compared("single") & (ref[:, 0] == oracle.EQUATOR)
+    assert sel.sum() >= 0.9 * (far & (ref[:, 0] == oracle.EQUATOR)).sum(), R.census()
+    rel = np.abs(rec32[sel, 5] - ref[sel, 5]) / ref[sel, 5]
+    assert rel.max() <= 1e-4
+    assert np.abs(P.wrap(rec32[sel, 7] - ref[sel, 7])).max() <= 1e-4
 
 
 def test_trace_split_over_calls_equals_one_call():
@@ -322,12 +327,19 @@ def test_ragged_sizes(n):
     rc, n_active, _ = tr.trace()
     rec = tr.records()
     tr.close()
-    ref = oracle.trace_many(rays, oracle.Options(max_steps=20000))
     assert rc == 0 and n_active == 0
-    same = rec[:, 0] == ref[:, 0]
-    assert same.mean() >= 0.99
-    ok = same & ((ref[:, 0] == 1) | (ref[:, 0] == 2))
-    assert np.median(np.abs(rec[ok, 6] - ref[ok, 6])) < 1e-9
+    # every ray outside its own 0.05 M band and not chaotic keeps the
+    # oracle's status; the double-conditioned ones its final angles to 1e-9
+    # with identical step counts
+    R = P.Reference(rays, oracle.Options(max_steps=20000), P.per_ray_far(rays[:, :4]), single=False,
+                    double=True)
+    ref = R.ref
+    settled = R.far & ~R.chaotic
+    assert np.all(rec[settled, 0] == ref[settled, 0])
+    sel = R.compared("double")
+    assert sel.sum() >= 0.9 * settled.sum(), R.census("double")
+    assert P.rel_move(rec, ref)[sel].max(initial=0.0) <= 1e-9
+    assert np.all(rec[sel, 1] == ref[sel, 1])
 
 
 def test_empty_and_degenerate():
