@@ -204,10 +204,10 @@ def cpu_sample_rays(im, n_sample):
     return rays
 
 
-def cpu_oracle_rate(im, max_steps, step_rule, n_sample):
+def cpu_oracle_rate(im, max_steps, step_rule, n_sample, threads=None):
     import oracle
     rays = cpu_sample_rays(im, n_sample)
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     t0 = time.perf_counter()
     out = oracle.trace_many(rays, oracle.Options(max_steps=max_steps, step_rule=step_rule), nthreads=cores)
     dt = time.perf_counter() - t0
@@ -742,6 +742,11 @@ def main():
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d evenly spread pixels of the %dx%d image (%.0f steps, %.1f s)" % (
                    ns, args.side, args.side, st, dt)}
+        # the same oracle on one core, on a 64x smaller sample
+        rate1, _, ns1, st1, dt1 = cpu_oracle_rate(im, 10000, 1 if rule == gray.STEP_EQ2 else 0,
+                                                  max(256, args.cpu_rays // 64), threads=1)
+        cpu["single_thread"] = {"value": rate1, "unit": UNIT, "cores": 1,
+                                "sample": "%d evenly spread pixels (%.0f steps, %.1f s)" % (ns1, st1, dt1)}
 
     if rank == 0:
         line = {

@@ -1,7 +1,9 @@
 """Acceptance of the tracer against the FP64 oracle, on the benchmark's
 workloads: the a = 0.99, i = 90 deg image (at 96^2 and 192^2, and at its
-full 1024^2 size in the bench's own launch configuration, on sampled pixels)
-and the mixed per-ray stream (2^16 rays, half near each ray's critical curve).
+full 1024^2 size in the bench's own launch configuration, on sampled pixels),
+the mixed per-ray stream (2^16 rays, half near each ray's critical curve, and
+its full 2^26 rays on sampled rays) and the batched 256-image sweep at full
+size (on sampled pixels).
 
 Which rays each tolerance covers is decided by the oracle alone (parity.py):
 classification on every ray outside the 0.05 M band; final angles on the
@@ -196,6 +198,80 @@ def test_full_size_bench_configuration_on_sampled_pixels():
     rec, inv, R = _full_size(gray.FP32_KAHAN_SEL64)
     c, f, cen = check_single(rec, inv, R, "full-size bench configuration", drift_tol=None)
     assert c["n_compared"] > 3500
+
+
+def _sampled_records(tr, idx):
+    """Records of the rays idx (ascending) of a tracer, one ray at a time
+    (the full record array of these workloads would not fit host memory)."""
+    return np.concatenate([tr.records(int(i), 1) for i in idx])
+
+
+def test_full_size_mixed_stream_on_sampled_rays():
+    """The mixed stream at its full size (2^26 rays, half within 0.1 M of
+    their critical curve) in the bench's launch configuration (per-ray set-up,
+    persistent refilling trace, compensated FP32 + zone r_sw = 0.02), on 4096
+    evenly spread rays: classification >= 99.99 % outside each ray's band,
+    and the final angles of the single-conditioned rays within 1e-4 rad (the
+    2^16-ray test's bounds); then FP64 on the bench's 1/16 subset, on 4096 of
+    its rays: the FP64 acceptance."""
+    n = 1 << 26
+    rays = I.mixed_rays(n)
+    idx = np.unique(np.linspace(0, n - 1, 4096).astype(np.int64))
+    dev = torch.as_tensor(rays, device="cuda")
+    tr = gray.Tracer(gray.Options(precision=gray.FP32_KAHAN_SEL64, max_steps=10000, r_sw=0.02), n)
+    tr.setup_rays(dev)
+    rc, n_active, stats = tr.trace()
+    assert rc == 0 and n_active == 0 and stats[2] > 0
+    rec = _sampled_records(tr, idx)
+    tr.close()
+    sub = rays[idx]
+    R = P.Reference(sub, oracle.Options(max_steps=10000), P.per_ray_far(sub), single=True, double=True)
+    c, f, cen = check_single(rec, None, R, "mixed 2^26 sampled", faithful_frac=5e-3, compared_frac=2e-4,
+                             captured_share=0.9, drift_tol=None)
+    assert c["n_compared"] > 2500
+    m = n // 16
+    idx64 = np.unique(np.linspace(0, m - 1, 4096).astype(np.int64))
+    tr = gray.Tracer(gray.Options(precision=gray.FP64, max_steps=10000), m)
+    tr.setup_rays(dev[:m].contiguous())
+    rc, n_active, _ = tr.trace()
+    assert rc == 0 and n_active == 0
+    rec64 = _sampled_records(tr, idx64)
+    inv64 = np.concatenate([tr.invariants(int(i), 1) for i in idx64])
+    tr.close()
+    del dev
+    sub = rays[idx64]
+    R64 = P.Reference(sub, oracle.Options(max_steps=10000), P.per_ray_far(sub), single=False, double=True)
+    c64, _ = check_double(rec64, inv64, R64, "mixed 2^22 FP64 sampled")
+    assert c64["n_compared"] > 2500
+
+
+def test_full_size_shadow_sweep_on_sampled_pixels():
+    """The batched sweep at its full size (256 images of side 64..1024,
+    1.0e8 rays) in the bench's launch configuration (one fused set-up and
+    plan, one persistent trace; compensated FP32 + zone r_sw = 0.02), on 16
+    evenly spread pixels of every image: classification >= 99.99 % outside
+    each image's band, no single-conditioned ray beyond 1e-4 rad."""
+    from paper_1303_5057_gb300 import batch
+    wl = I.shadow_sweep(n_images=256)
+    sw = batch.ShadowSweep(wl.images, gray.Options(precision=gray.FP32_KAHAN_SEL64, max_steps=10000, r_sw=0.02),
+                           plan=True, probe_stride=6, probe_budget=400)
+    sw.run()
+    rows, recs, fars, first = [], [], [], 0
+    for im in wl.images:
+        k = np.unique(np.linspace(0, im.n - 1, 16).astype(np.int64))
+        rays = oracle.image_rays(im.a, im.incl, im.r_obs, im.nx, im.ny, im.alpha0, im.alpha1, im.beta0,
+                                 im.beta1)[k]
+        rows.append(rays)
+        fars.append(P.band_mask((rays[:, 0], rays[:, 1]), im.a, max(im.incl, 1e-3)))
+        recs.append(_sampled_records(sw.tracer, first + k))
+        first += im.n
+    sw.close()
+    rays = np.concatenate(rows)
+    rec = np.concatenate(recs)
+    far = np.concatenate(fars)
+    R = P.Reference(rays, oracle.Options(max_steps=10000), far, single=True)
+    c, f, cen = check_single(rec, None, R, "sweep sampled", drift_tol=None, captured_share=0.9)
+    assert c["n_compared"] > 3000
 
 
 # ------------------------------------------------- single precision, images ---
