@@ -199,7 +199,8 @@ struct ImageDev {
     double b0, db; // Cartesian: beta likewise; polar: first angle, angle step
     long long first; // first ray of the image relative to the call's first ray
     int nx, ny;
-    int grid, pad;
+    int grid;
+    int probe_first; // planning: the image's first probe among the call's probes (0 otherwise)
     float hc[8]; // single-precision per-ray constants (hole_constants_f), once per image
 };
 static_assert(sizeof(ImageDev) == 136, "gray_setup_noalloc's table size is documented in gray.h");
@@ -1223,8 +1224,8 @@ __global__ void count_active_kernel(const int4 *S0, int64_t n, unsigned long lon
 // lumped into one top bucket (measured: 8.06 -> 8.00 ms single-precision
 // pass against 64 buckets over 0 .. 2 budget).
 constexpr int PLAN_BUCKETS = 1024;
-// aux layout: [0] probe count, [1 ..] histogram, [1 + PLAN_BUCKETS ..] bucket offsets
-constexpr int AUX_PROBES = 0, AUX_HIST = 1, AUX_OFF = 1 + PLAN_BUCKETS, AUX_WORDS = 1 + 2 * PLAN_BUCKETS;
+// aux layout: [0] unused, [1 ..] histogram, [1 + PLAN_BUCKETS ..] bucket offsets
+constexpr int AUX_HIST = 1, AUX_OFF = 1 + PLAN_BUCKETS, AUX_WORDS = 1 + 2 * PLAN_BUCKETS;
 // one more word after the planning words: the call epoch (never cleared)
 constexpr int AUX_EPOCH = AUX_WORDS, AUX_CANCEL = AUX_WORDS + 1, AUX_ALLOC = AUX_WORDS + 2;
 
@@ -1248,26 +1249,36 @@ __device__ __forceinline__ int image_of(const ImageDev *imgs, int n_images, int6
     return lo;
 }
 
-__global__ void probe_list_kernel(const ImageDev *imgs, int n_images, int64_t total, int64_t first_ray, int stride,
-                                  int *list, unsigned long long *aux)
+// The probe rays of the planning pass (every stride-th pixel of every stride-th
+// row of each image), one thread per probe: its queue entry, and with `setup`
+// its initial state as setup_images_kernel writes it.  Probe q of the call
+// lies in the last image with probe_first <= q.
+__global__ void probe_rays_kernel(const ImageDev *imgs, int n_images, int64_t n_probes, int64_t first_ray,
+                                  int stride, int *order, StateView v, int prec, int setup)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool probe = false;
-    if (i < total) {
-        const ImageDev im = imgs[image_of(imgs, n_images, i)];
-        const int64_t p = i - im.first, row = p / im.nx, col = p - row * im.nx;
-        probe = (row % stride == 0) && (col % stride == 0);
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, probe);
-    if (!m)
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_probes)
         return;
-    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-    unsigned long long base = 0;
-    if (lane == leader)
-        base = atomicAdd(&aux[AUX_PROBES], (unsigned long long)__popc(m));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (probe)
-        list[base + __popc(m & ((1u << lane) - 1u))] = (int)(first_ray + i);
+    int lo = 0, hi = n_images - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (imgs[mid].probe_first <= q)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const ImageDev im = imgs[lo];
+    const int64_t per_row = (im.nx + stride - 1) / stride;
+    const int64_t k = q - im.probe_first, row = (k / per_row) * stride, col = (k % per_row) * stride;
+    const int64_t i = im.first + row * im.nx + col;
+    order[q] = (int)(first_ray + i);
+    if (setup) {
+        double alpha, beta;
+        image_point(im, row, col, alpha, beta);
+        double y[8];
+        initial_state_sc(im.M, im.a, im.r_obs, im.si, im.ci, alpha, beta, y);
+        store_initial(v, prec, first_ray + i, y, im.a, im.M, im.r_obs, im.hc);
+    }
 }
 
 // Predicted cost of pixel i: the largest probe cost among the 4 x 4 probes
@@ -2020,7 +2031,7 @@ ImageDev image_dev(const gray_image &im, int64_t first)
     d.nx = im.nx;
     d.ny = im.ny;
     d.grid = im.grid;
-    d.pad = 0;
+    d.probe_first = 0;
     hole_constants_f(im.a, im.M, im.r_obs, d.hc);
     return d;
 }
@@ -2416,7 +2427,7 @@ namespace {
 // table and its ray count.
 int plan_args(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, const gray_image *images,
               int32_t n_images, int64_t first_ray, int32_t probe_stride, int32_t probe_budget, int32_t *order,
-              size_t order_bytes, std::vector<ImageDev> &t, int64_t &total)
+              size_t order_bytes, std::vector<ImageDev> &t, int64_t &total, int64_t &n_probes)
 {
     int rc = check_state(ctx, state, state_bytes, n_state);
     if (rc)
@@ -2430,23 +2441,32 @@ int plan_args(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, c
     t = image_table(images, n_images, total);
     if (first_ray + total > n_state || order_bytes < sizeof(int32_t) * (size_t)total)
         return GRAY_EINVAL;
+    // each image's probes: ceil(nx / stride) per probe row, ceil(ny / stride) rows
+    n_probes = 0;
+    for (int k = 0; k < n_images; ++k) {
+        t[(size_t)k].probe_first = (int)n_probes;
+        n_probes += (int64_t)((images[k].nx + probe_stride - 1) / probe_stride) *
+                    ((images[k].ny + probe_stride - 1) / probe_stride);
+    }
     return GRAY_OK;
 }
 
 // The planning passes on stream s (image table `im` already on the device):
-// 1. the probe list (written into the order buffer), 2. the probes traced
-// under the probe budget, 3. predicted cost -> bucket histogram ->
-// descending offsets -> queue.  Only the probe rays' states are read.
-int plan_passes(gray_ctx *ctx, void *state, int64_t n_state, const gray_image *images, int32_t n_images,
-                const ImageDev *im, int64_t total, int64_t first_ray, int32_t probe_stride, int32_t probe_budget,
-                int32_t *order, cudaStream_t s)
+// 1. the probe list (written into the order buffer; with setup_probes the
+// probe rays are set up in the same pass), 2. the probes traced under the
+// probe budget, 3. predicted cost -> bucket histogram -> descending offsets
+// -> queue.  Only the probe rays' states are read.
+int plan_passes(gray_ctx *ctx, void *state, int64_t n_state, int32_t n_images, const ImageDev *im, int64_t total,
+                int64_t n_probes, int64_t first_ray, int32_t probe_stride, int32_t probe_budget, int32_t *order,
+                bool setup_probes, cudaStream_t s)
 {
     int rc;
     if (cudaMemsetAsync(ctx->aux, 0, AUX_WORDS * sizeof(unsigned long long), s) != cudaSuccess ||
         cudaMemsetAsync(ctx->ws, 0, sizeof(Workspace), s) != cudaSuccess)
         return GRAY_ECUDA;
-    probe_list_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, probe_stride, order,
-                                                          ctx->aux);
+    const StateView v = make_view(state, n_state, ctx->opt.precision);
+    probe_rays_kernel<<<grid_for(n_probes, 128), 128, 0, s>>>(im, n_images, n_probes, first_ray, probe_stride, order,
+                                                             v, ctx->opt.precision, setup_probes ? 1 : 0);
     if ((rc = check_launch()))
         return rc;
     bump_epoch_kernel<<<1, 1, 0, s>>>(ctx->aux);
@@ -2454,21 +2474,16 @@ int plan_passes(gray_ctx *ctx, void *state, int64_t n_state, const gray_image *i
         return rc;
     TraceArgs A = make_trace_args(ctx, state, n_state, probe_budget);
     A.order = order;
-    A.n_queue_dev = &ctx->aux[AUX_PROBES];
+    A.n_queue = n_probes;
     ctx->ev_used[2] = false;
     if (ctx->timing) {
         cudaEventRecord(ctx->ev[4], s);
         ctx->ev_used[2] = true;
     }
-    int64_t probes_max = 0;
-    for (int k = 0; k < n_images; ++k)
-        probes_max += (int64_t)((images[k].nx + probe_stride - 1) / probe_stride) *
-                      ((images[k].ny + probe_stride - 1) / probe_stride);
-    if ((rc = launch_pass(ctx, A, probes_max, s)))
+    if ((rc = launch_pass(ctx, A, n_probes, s)))
         return rc;
     if (ctx->timing)
         cudaEventRecord(ctx->ev[5], s);
-    const StateView v = make_view(state, n_state, ctx->opt.precision);
     plan_hist_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, probe_stride, probe_budget,
                                                          v.S0, ctx->aux);
     if ((rc = check_launch()))
@@ -2490,17 +2505,17 @@ int gray_plan(gray_ctx *ctx, void *state, size_t state_bytes, int64_t n_state, c
               size_t order_bytes, void *stream)
 {
     std::vector<ImageDev> t;
-    int64_t total = 0;
+    int64_t total = 0, n_probes = 0;
     int rc = plan_args(ctx, state, state_bytes, n_state, images, n_images, first_ray, probe_stride, probe_budget,
-                       order, order_bytes, t, total);
+                       order, order_bytes, t, total, n_probes);
     if (rc)
         return rc;
     cudaStream_t s = (cudaStream_t)stream;
     void *dimg = nullptr;
     if ((rc = upload_table(t.data(), t.size() * sizeof(ImageDev), s, &dimg)))
         return rc;
-    rc = plan_passes(ctx, state, n_state, images, n_images, (const ImageDev *)dimg, total, first_ray, probe_stride,
-                     probe_budget, order, s);
+    rc = plan_passes(ctx, state, n_state, n_images, (const ImageDev *)dimg, total, n_probes, first_ray, probe_stride,
+                     probe_budget, order, false, s);
     cudaError_t e = cudaFreeAsync(dimg, s);
     if (rc)
         return rc;
@@ -2512,9 +2527,9 @@ int gray_setup_plan(gray_ctx *ctx, const gray_image *images, int32_t n_images, v
                     size_t order_bytes, void *stream)
 {
     std::vector<ImageDev> t;
-    int64_t total = 0;
+    int64_t total = 0, n_probes = 0;
     int rc = plan_args(ctx, state, state_bytes, n_state, images, n_images, first_ray, probe_stride, probe_budget,
-                       order, order_bytes, t, total);
+                       order, order_bytes, t, total, n_probes);
     if (rc)
         return rc;
     int least = 0, greatest = 0;
@@ -2530,20 +2545,17 @@ int gray_setup_plan(gray_ctx *ctx, const gray_image *images, int32_t n_images, v
         return rc;
     const ImageDev *im = (const ImageDev *)dimg;
     StateView v = make_view(state, n_state, ctx->opt.precision);
-    // the probe rays first, on the caller's stream
-    setup_images_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, v, ctx->opt.precision,
-                                                           probe_stride, 1);
-    rc = check_launch();
-    // the planning passes on the context's high-priority stream, after
-    // everything queued so far on the caller's stream; the other rays' set-up
-    // (bound by the double-precision pipe) fills the SMs the probe pass (few,
+    // the probe rays' set-up and the planning passes on the context's
+    // high-priority stream, after everything queued so far on the caller's
+    // stream (the image table); meanwhile the other rays' set-up (bound by
+    // the double-precision pipe) fills the SMs that the probe pass (few,
     // latency-bound warps) leaves free
-    if (!rc) {
+    {
         if (cudaEventRecord(ctx->fork, s) != cudaSuccess || cudaStreamWaitEvent(ctx->side, ctx->fork, 0) != cudaSuccess) {
             rc = GRAY_ECUDA;
         } else {
-            rc = plan_passes(ctx, state, n_state, images, n_images, im, total, first_ray, probe_stride, probe_budget,
-                             order, ctx->side);
+            rc = plan_passes(ctx, state, n_state, n_images, im, total, n_probes, first_ray, probe_stride, probe_budget,
+                             order, true, ctx->side);
             const bool joined = cudaEventRecord(ctx->join, ctx->side) == cudaSuccess;
             if (!rc) {
                 setup_images_kernel<<<grid_for(total, 256), 256, 0, s>>>(im, n_images, total, first_ray, v,
