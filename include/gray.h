@@ -257,10 +257,10 @@ int gray_plan(gray_ctx *ctx, void *state_dev, size_t state_bytes, int64_t n_stat
               void *stream);
 
 /* gray_setup followed by gray_plan with the same images, first_ray, probe
- * stride and budget, in one call: the probe rays are set up first on
- * `stream`; the planning passes then run on a high-priority stream of the
- * context (after everything queued so far on `stream`) while the other
- * rays are set up on `stream` (the set-up is bound by the double-precision
+ * stride and budget, in one call: the probe rays' set-up and the planning
+ * passes run on a high-priority stream of the context (after everything
+ * queued so far on `stream`) while the other rays are set up on `stream`
+ * (the set-up is bound by the double-precision
  * pipe, the probe pass by single-precision issue and latency, so the two
  * share the SMs).  `stream` waits for the plan before the call's last
  * operation, so work queued on it afterwards sees every ray set up and the
