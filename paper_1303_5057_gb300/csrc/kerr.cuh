@@ -720,20 +720,12 @@ __device__ __forceinline__ void geodesic_accel(const Hole<T> &H, T r, T th, T kt
 template <typename T> __device__ __forceinline__ T step_size(const Hole<T> &H, const StepOpt<T> &O, const T *y)
 {
     const T r = y[1], kr = y[5];
-    T guard, h;
-    if (sizeof(T) == 4) {
-        guard = (r - H.r_h) * (T(0.5) * recip(fabs(kr)));
-        if (O.step_rule == 1)
-            h = fmin(O.h_frac * recip(fabs(kr) * recip(r) + fabs(y[6]) + fabs(y[7])), guard);
-        else
-            h = fmin(O.h_frac * r, guard);
-    } else {
-        guard = (r - H.r_h) * (T(0.5) * recip(fabs(kr)));
-        if (O.step_rule == 1)
-            h = fmin(O.h_frac * recip(fabs(kr) * recip(r) + fabs(y[6]) + fabs(y[7])), guard);
-        else
-            h = fmin(O.h_frac * r, guard);
-    }
+    const T guard = (r - H.r_h) * (T(0.5) * recip(fabs(kr)));
+    T h;
+    if (O.step_rule == 1)
+        h = fmin(O.h_frac * recip(fabs(kr) * recip(r) + fabs(y[6]) + fabs(y[7])), guard);
+    else
+        h = fmin(O.h_frac * r, guard);
     h = fmax(h, O.h_min);
     return -h;
 }
