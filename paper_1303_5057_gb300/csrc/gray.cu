@@ -2,8 +2,12 @@
 //
 // Kernels:
 //   setup_images_kernel / setup_rays_kernel  image-plane initial conditions (double)
-//   trace_kernel<MODE>                       persistent backward RK4 tracer
-//   render_kernel, shadow_*_kernel           read-out of results
+//   trace32_kernel<MODE>, trace64_kernel     persistent backward RK4 tracers
+//                                            (single precision, double)
+//   zone_kernel<RETURN, T>                   the near-horizon zone of the
+//                                            selective mode (double-single or double)
+//   probe_rays_kernel, plan_*_kernel         the longest-first planner
+//   render_kernel, shadow_*, ring_*, splat   read-out of results
 //   eval_kernel<T>                           unit evaluations for parity tests
 //
 // Trace kernel design (GRay Sec. 2 puts one photon in one thread; here a
@@ -99,7 +103,7 @@ Layout make_layout(int64_t n, int prec)
     L.L = off;
     off = align256(off + 4 * un);
     if (prec == GRAY_FP32_KAHAN_SEL64) {
-        L.R = off; // rays the double zone returns to single precision
+        L.R = off; // rays the zone pass returns to single precision
         off = align256(off + 4 * un);
     } else {
         L.R = 0;
@@ -540,16 +544,18 @@ __device__ __forceinline__ int step_once(const Hole<T> &H, const StepOpt<T> &O, 
 // --------------------------------------------------------------------------
 //
 // Single-precision modes run trace32_kernel over every ray of the buffer.
-// In GRAY_FP32_KAHAN_SEL64 a ray that reaches the double zone (r below
+// In GRAY_FP32_KAHAN_SEL64 a ray that reaches the zone (r below
 // cap_frac r_h + r_sw at the start of a step) is handed off: its state is
-// stored and its index appended to the hand-off list.  trace64_kernel then
-// runs the listed rays in double precision, 32 to a warp, until they stop
-// or climb out of the zone (r above cap_frac r_h + 2 r_sw), when they return
-// to single precision for the next pass.  The FP64 pipe of this part runs at
-// 1/64 of the FP32 rate, so a double step must never hold a warp of
-// single-precision lanes; the hand-off keeps the two populations apart and
-// the single-precision kernel free of double-precision registers.
-// GRAY_FP64 runs trace64_kernel over every ray, with double planes.
+// stored and its index appended to the hand-off list.  zone_kernel then
+// runs the listed rays in extended precision (double-single by default,
+// IEEE double as an option), 32 to a warp, until they stop or climb out of
+// the zone (r above cap_frac r_h + 2 r_sw), when they return to single
+// precision for the next pass.  The zone's arithmetic is ~8 times longer
+// per step (and the FP64 pipe of this part runs at 1/64 of the FP32 rate),
+// so a zone step must never hold a warp of single-precision lanes; the
+// hand-off keeps the two populations apart and the single-precision kernel
+// free of the zone's registers.  GRAY_FP64 runs trace64_kernel over every
+// ray, with double planes.
 
 enum : int { FLAG_DOUBLE_MODE = 1, FLAG_DOUBLE_REPR = 2 };
 
@@ -715,7 +721,7 @@ template <int MODE, int MAXREG = 128> __global__ void __maxnreg__(MAXREG) trace3
                     if (s0.x == GRAY_RAY_ACTIVE) {
                         const int4 s1 = v.S1[my];
                         if (SEL64 && (s1.w & FLAG_DOUBLE_MODE)) {
-                            handoff_now = true; // resumed inside the double zone
+                            handoff_now = true; // resumed inside the zone
                             id = my;
                         } else {
                             has = true;
@@ -1023,7 +1029,7 @@ __global__ void __launch_bounds__(128, RETURN ? 3 : 1) zone_kernel(TraceArgs A)
                                              (float)A.r_sw);
                         r_demote = Hd.r_promote + r_sw;
                         if (s1.w & FLAG_DOUBLE_REPR) {
-                            // exact double state parked in the four single planes (double zone)
+                            // exact double state parked in the four single planes (IEEE-double zone)
                             const double2 q0 = ((const double2 *)v.X)[my], q1 = ((const double2 *)v.K)[my];
                             const double2 q2 = ((const double2 *)v.CX)[my], q3 = ((const double2 *)v.CK)[my];
                             const double q[8] = {q0.x, q0.y, q1.x, q1.y, q2.x, q2.y, q3.x, q3.y};
