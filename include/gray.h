@@ -221,20 +221,22 @@ int gray_setup_rays(gray_ctx *ctx, const double *rays_dev, int64_t n, double M,
  * on its place in the queue.  If n_active_host is not NULL the call waits for
  * the stream and stores the number of rays of the buffer still active; if
  * stats_host is not NULL (4 int64) it stores, for this call: steps taken,
- * Euler redos, steps taken in double by the selective mode, rays still
+ * Euler redos, steps taken in the zone by the selective mode, rays still
  * active.  Returns 0 when no ray is active, 1 when some remain or when no
  * host output was requested (the count is then unknown), or an error
  * (GRAY_EINVAL, GRAY_ECUDA).
  * In GRAY_FP32_KAHAN_SEL64 the call makes a single-precision pass over the
- * queue, then a double-precision pass over the rays that entered the zone
- * near the horizon (rays climbing out of it are returned to a single-precision
- * pass), then a last zone pass for the rays that came back to the zone (in
- * double there, in compensated single precision once they leave it).  A ray's
- * arithmetic does not depend on which pass runs it.  The zone r < cap_frac r_h
- * + r_sw keeps the final angles of captured rays within 1e-4 rad of the FP64
- * arithmetic at r_sw = 0.02 but for a few rays that cross the ergosurface,
- * where the single-precision Eq. 4 test cannot resolve its threshold;
- * r_sw = 0.9 (the ergoregion at the equator) removes those at ~3x the time. */
+ * queue, then a pass in the zone's extended precision (zone_arith) over the
+ * rays that entered the zone near the horizon (rays climbing out of it are
+ * returned to a single-precision pass), then a last zone pass for the rays
+ * that came back to the zone (in the zone's arithmetic there, in compensated
+ * single precision once they leave it).  A ray's arithmetic does not depend
+ * on which pass runs it.  Inside the single-precision pass, an Eq. 4 test
+ * whose outcome lies within single precision's rounding of its threshold
+ * (near the ergosurface, where g_tt vanishes) is taken again in double-single
+ * arithmetic.  With r_sw = 0.02 the final angles of every ray whose result
+ * is conditioned at single precision stay within 1e-4 rad of the FP64
+ * oracle's, captured rays included. */
 int gray_trace(gray_ctx *ctx, void *state_dev, size_t state_bytes, int64_t n_state,
                const int32_t *order_dev, int64_t n_order, int64_t step_budget,
                int64_t *n_active_host, int64_t *stats_host, void *stream);
