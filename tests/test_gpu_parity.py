@@ -391,6 +391,32 @@ def test_planned_order_gives_identical_results(prec):
     assert np.array_equal(want, got)
 
 
+@pytest.mark.parametrize("stride", [1, 4, 100])
+def test_fused_plan_sets_up_and_queues_every_ray_for_any_stride(stride):
+    """gray_setup_plan with images of very different sizes (one pixel, a
+    ragged 7 x 3 and 40 x 33) and probe strides from 1 (every pixel a probe)
+    to beyond every image's side (one probe per image): the queue is a
+    permutation of the rays, and the planned trace (probes set up and traced
+    on the planning stream, the other rays set up beside them) equals
+    gray_setup + a natural-order trace bit for bit."""
+    ims = [I.Image(a=0.9, incl=1.0, nx=1, ny=1, alpha0=3.0, alpha1=3.5, beta0=1.0, beta1=1.5),
+           I.Image(a=0.5, incl=0.7, nx=7, ny=3), I.Image(a=0.99, incl=1.5, nx=40, ny=33)]
+    n = sum(im.n for im in ims)
+    opt = gray.Options(precision=gray.FP32_KAHAN_SEL64, max_steps=10000, r_sw=0.02)
+    ref = gray.Tracer(opt, n)
+    ref.setup(ims)
+    ref.trace()
+    want = ref.records()
+    ref.close()
+    tr = gray.Tracer(opt, n + 2)
+    order = tr.setup_plan(ims, first_ray=2, probe_stride=stride, probe_budget=60)
+    o = order.cpu().numpy()
+    assert np.array_equal(np.sort(o), np.arange(2, 2 + n))
+    tr.trace(order=order)
+    assert np.array_equal(tr.records(first_ray=2, n=n), want)
+    tr.close()
+
+
 @pytest.mark.parametrize("prec", [gray.FP32_KAHAN, gray.FP32_KAHAN_SEL64])
 def test_one_ray_per_thread_launch_equals_persistent(prec):
     """The paper's launch (Eq. 1: one ray per thread, blocks of 64) and the
