@@ -160,13 +160,14 @@ def test_kerr_fp64_matches_oracle(rule):
     check_double(rec, inv, R, "kerr96 rule %d" % rule)
 
 
-def _full_size(prec, n_sample=4096):
+def _full_size(prec, n_sample=4096, rule=gray.STEP_BENCH, r_sw=0.02):
     """The bench workload at full size (a = 0.99, i = 90 deg, 1024^2, cap 1e4)
     in the bench's launch configuration (set-up fused with the stride-6,
-    budget-400 plan; persistent trace; r_sw = 0.02), the records of
-    n_sample evenly spread pixels, and the oracle Reference of those pixels."""
+    budget-400 plan; persistent trace; r_sw = 0.02 unless given), the records
+    of n_sample evenly spread pixels, and the oracle Reference of those
+    pixels."""
     im = I.kerr_1024(1024).images[0]
-    tr = gray.Tracer(gray.Options(precision=prec, max_steps=10000, r_sw=0.02), im.n)
+    tr = gray.Tracer(gray.Options(precision=prec, max_steps=10000, r_sw=r_sw, step_rule=rule), im.n)
     order = tr.setup_plan([im], probe_stride=6, probe_budget=400)
     rc, n_active, _ = tr.trace(order=order)
     rec = tr.records()
@@ -174,12 +175,13 @@ def _full_size(prec, n_sample=4096):
     tr.close()
     assert rc == 0 and n_active == 0
     idx = np.unique(np.linspace(0, im.n - 1, n_sample).astype(np.int64))
-    key = ("full", n_sample)
+    key = ("full", n_sample, rule)
     if key not in _CACHE:
         rays = oracle.image_rays(im.a, im.incl, im.r_obs, im.nx, im.ny, im.alpha0, im.alpha1, im.beta0,
                                  im.beta1)[idx]
         far = P.band_mask((rays[:, 0], rays[:, 1]), im.a, im.incl)
-        _CACHE[key] = P.Reference(rays, oracle.Options(max_steps=10000), far, single=True, double=True)
+        _CACHE[key] = P.Reference(rays, oracle.Options(max_steps=10000, step_rule=rule), far, single=True,
+                                  double=True)
     return rec[idx], inv[idx], _CACHE[key]
 
 
@@ -272,6 +274,19 @@ def test_full_size_shadow_sweep_on_sampled_pixels():
     R = P.Reference(rays, oracle.Options(max_steps=10000), far, single=True)
     c, f, cen = check_single(rec, None, R, "sweep sampled", drift_tol=None, captured_share=0.9)
     assert c["n_compared"] > 3000
+
+
+def test_full_size_eq2_on_sampled_pixels():
+    """The paper's Eq. 2 step rule at the bench image's full size and launch
+    configuration, on 4096 sampled pixels: FP64 to 1e-9 with identical step
+    counts, and compensated FP32 with the zone over 1 M (as at 96^2) with no
+    conditioned ray beyond 1e-4 rad."""
+    rec, inv, R = _full_size(gray.FP64, rule=gray.STEP_EQ2)
+    c, cen = check_double(rec, inv, R, "full-size eq2")
+    assert c["n_compared"] > 3500
+    rec, inv, R = _full_size(gray.FP32_KAHAN_SEL64, rule=gray.STEP_EQ2, r_sw=1.0)
+    c, f, cen = check_single(rec, inv, R, "full-size eq2 r_sw 1", drift_tol=None)
+    assert c["n_compared"] > 3500
 
 
 # ------------------------------------------------- single precision, images ---
