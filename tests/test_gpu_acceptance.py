@@ -390,7 +390,7 @@ def test_mixed_stream_compensated_single_precision(prec):
     rays, R = mixed_reference()
     rec, inv, _ = trace_rays(rays, gray.Options(precision=prec, max_steps=10000, r_sw=0.02))
     # half of these rays lie within 0.1 M of their critical curve: a few
-    # conditioned ones (measured 5 in 47206) still leave 1e-4 rad
+    # conditioned ones (measured: at most 4 of 47206) still leave 1e-4 rad
     c, f, cen = check_single(rec, inv, R, "mixed prec %d" % prec, faithful_frac=5e-3, compared_frac=2e-4,
                              captured_share=0.9)
     assert c["n_compared"] > 40000
